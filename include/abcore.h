@@ -1,0 +1,187 @@
+/*
+ * abcore.h -- exact (alpha, beta)-core computation on bipartite graphs, on one GB300 (sm_103a).
+ *
+ * A bipartite graph G = (U u L, E) with E a subset of U x L (Section 3 of the paper) is loaded
+ * once onto the GPU. The (alpha, beta)-core (Definition 1) is the maximal vertex set in which
+ * every upper (U) vertex has at least alpha neighbours and every lower (L, here "V") vertex
+ * has at least beta neighbours inside the set. It is unique, so every result of this library
+ * is exact and bit-for-bit reproducible: a membership mask byte is 1 for a member, 0 otherwise.
+ *
+ * Conventions for every call:
+ *  - Return value: ABCORE_OK (0) or a negative ABCORE_E* code. After an error,
+ *    abcore_last_error(ctx) describes it; the context stays usable unless the code is
+ *    ABCORE_ECUDA.
+ *  - Vertex ids at the interface are per layer: u in [0, nU), v in [0, nV).
+ *  - Pointer arguments are host pointers unless the call's flags contain ABCORE_PTR_DEVICE, in
+ *    which case they are device pointers on the context's device. The caller owns every buffer
+ *    it passes; the library copies inputs and never keeps a caller pointer after returning.
+ *  - All device work is ordered on the context's stream. Calls block until their results are
+ *    ready, except abcore_compute / abcore_compute_batch with ABCORE_PTR_DEVICE | ABCORE_ASYNC,
+ *    which return once the work is enqueued; abcore_sync then waits and reports its status.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef ABCORE_H
+#define ABCORE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define ABCORE_OK           0
+#define ABCORE_EINVAL     (-1)  /* bad argument: negative threshold, id out of range, ...      */
+#define ABCORE_ENOTLOADED (-2)  /* no graph has been loaded into the context                  */
+#define ABCORE_ENOMEM     (-3)  /* device or host allocation failed                           */
+#define ABCORE_EEXIST     (-4)  /* insert of an edge already present / duplicate input edge   */
+#define ABCORE_ENOENT     (-5)  /* delete of an edge that is not present                      */
+#define ABCORE_ECUDA      (-6)  /* a CUDA runtime call failed                                 */
+#define ABCORE_ETIMEDOUT  (-7)  /* a bounded device-side wait expired; the work was abandoned */
+#define ABCORE_EBUSY      (-8)  /* request ring full; retry after polling completions         */
+
+/* ---- flags ----------------------------------------------------------------------------- */
+#define ABCORE_PTR_HOST   0u    /* pointer arguments are host memory (default)               */
+#define ABCORE_PTR_DEVICE 1u    /* pointer arguments are device memory of the ctx's device   */
+#define ABCORE_VALIDATE   2u    /* load: check the second CSR layer against the first         */
+#define ABCORE_ASYNC      4u    /* compute with device pointers: return after enqueueing      */
+
+/* ---- edge update kinds (abcore_query_edge, abcore_req.op) ------------------------------ */
+#define ABCORE_INSERT 0
+#define ABCORE_DELETE 1
+
+typedef struct abcore_ctx abcore_ctx;
+
+/* Per-call device counters of the last abcore_compute / abcore_compute_batch, plus memory. */
+typedef struct {
+    int64_t init_vertices;   /* candidate vertices whose in-candidate degree was set           */
+    int64_t search_probes;   /* adjacency words read while counting in-candidate neighbours     */
+    int64_t stream_entries;  /* adjacency entries streamed from the initial violators' rows     */
+    int64_t entries;         /* adjacency entries read by the cascade                           */
+    int64_t decrements;      /* atomic degree decrements issued                                 */
+    int64_t pushes;          /* vertices queued for removal after the initial scan              */
+    int64_t items;           /* cascade work items (row chunks) processed                       */
+    int64_t candidates;      /* |P|: vertices that met their bound on full degree               */
+    int64_t steps;           /* batch: chain steps executed                                     */
+    int32_t mode;            /* bit 0: U counts by search, bit 1: V counts by search            */
+    int32_t grid_blocks;     /* blocks of the persistent cascade launch                         */
+    int64_t device_bytes;    /* device memory currently held by the context                     */
+    int64_t peak_device_bytes;
+} abcore_stats;
+
+/* ---- lifecycle ------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to order all work
+ * on, or NULL for a stream the context creates and owns. *out receives the context. */
+int abcore_create(abcore_ctx **out, int device, void *cuda_stream);
+
+/* Release every device and host resource of the context. NULL is accepted. */
+int abcore_destroy(abcore_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Valid until the next call on ctx. */
+const char *abcore_last_error(abcore_ctx *ctx);
+
+/* ---- graph loading (Section 3: CSR storage; Section 4.1: flat continuous ids) ----------- */
+
+/* Load a graph from m distinct edges (eu[i], ev[i]), eu[i] in [0,nU), ev[i] in [0,nV).
+ * The device CSR builder stores both layers (U->V rows and V->U rows, int64 offsets, int32
+ * ids, each row sorted), renumbering vertices within each layer by non-increasing degree;
+ * results are always reported in the caller's ids. Replaces any previously loaded graph.
+ * Errors: EINVAL (negative sizes, id out of range), EEXIST (an edge given twice), ENOMEM. */
+int abcore_load_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64_t m,
+                      const int32_t *eu, const int32_t *ev, uint32_t flags);
+
+/* Load a graph given as the CSR of the U layer: offU[nU+1] (offU[0] = 0, non-decreasing),
+ * adjU[offU[nU]] holding V ids. offV/adjV (the V layer, U ids) may be NULL; when given with
+ * ABCORE_VALIDATE they must describe the same edge set, else EINVAL. Rows need not be
+ * sorted. Same errors as abcore_load_edges. */
+int abcore_load_csr(abcore_ctx *ctx, int32_t nU, int32_t nV,
+                    const int64_t *offU, const int32_t *adjU,
+                    const int64_t *offV, const int32_t *adjV, uint32_t flags);
+
+/* ---- (alpha, beta)-core computation (Definition 1; Algorithm 1, the GCC peel) ----------- */
+
+/* Compute the (alpha, beta)-core of the loaded graph. mask_u[nU] and mask_v[nV] receive one
+ * byte per vertex: 1 if in the core, else 0. alpha, beta >= 0 (0 = no constraint on that
+ * layer). Errors: EINVAL (negative threshold, NULL mask), ENOTLOADED, ETIMEDOUT. */
+int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta,
+                   uint8_t *mask_u, uint8_t *mask_v, uint32_t flags);
+
+/* Compute n cores at once (Lemma 1 and Algorithm 2 generalised: pairs sharing alpha are peeled
+ * as one chain of increasing beta, each core seeded from the one containing it). Pair i is
+ * (alphas[i], betas[i]); its masks are rows i of masks_u (n x nU, row-major) and masks_v
+ * (n x nV). Results equal n separate abcore_compute calls, whatever the pair order. The
+ * launch is captured once as a CUDA graph per pair list and replayed on later calls.
+ * Errors: as abcore_compute. */
+int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
+                         uint8_t *masks_u, uint8_t *masks_v, uint32_t flags);
+
+/* Wait for work enqueued with ABCORE_ASYNC and return its status. */
+int abcore_sync(abcore_ctx *ctx);
+
+/* ---- on-the-fly query (Section 5, GFQ) --------------------------------------------------- */
+
+/* Apply the edge update (u, v) -- op ABCORE_INSERT or ABCORE_DELETE -- to the loaded graph
+ * (it persists), then set *in_core to 1 iff both u and v belong to the (alpha, beta)-core of
+ * the updated graph, else 0. Only the region the update can affect is re-peeled.
+ * Errors: EINVAL, ENOTLOADED, EEXIST (insert of a present edge), ENOENT (delete of an
+ * absent edge); on those the graph is unchanged. */
+int abcore_query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta,
+                      uint8_t *in_core);
+
+/* ---- serving: continuously batched update/query stream ---------------------------------- */
+
+typedef struct {
+    int32_t op;       /* ABCORE_INSERT or ABCORE_DELETE                                  */
+    int32_t u, v;     /* per-layer endpoint ids                                          */
+    int32_t target;   /* index into the targets given to abcore_serve_start              */
+    uint64_t tag;     /* caller's value, echoed in the response                          */
+} abcore_req;
+
+typedef struct {
+    uint64_t seq;     /* arrival sequence number assigned by abcore_serve_submit          */
+    uint64_t tag;     /* the request's tag                                                */
+    int32_t status;   /* ABCORE_OK, ABCORE_EEXIST or ABCORE_ENOENT                        */
+    uint8_t in_core;  /* both endpoints in the target core after this update              */
+    uint8_t u_in;     /* u in the target core after this update                          */
+    uint8_t v_in;     /* v in the target core after this update                          */
+    uint8_t pad;
+} abcore_resp;
+
+/* Start serving with n_targets (alpha, beta) targets and a request ring of ring_slots entries.
+ * Updates are applied in submission order and every answer is the one the update would get
+ * if requests were processed one at a time, so answers do not depend on timing or batching. */
+int abcore_serve_start(abcore_ctx *ctx, const int32_t *target_alphas, const int32_t *target_betas,
+                       int32_t n_targets, int32_t ring_slots);
+
+/* Submit n requests; seq_out[i] (may be NULL) receives their sequence numbers. Returns EBUSY,
+ * submitting nothing, if the ring lacks room for all n. */
+int abcore_serve_submit(abcore_ctx *ctx, const abcore_req *reqs, int32_t n, uint64_t *seq_out);
+
+/* Copy up to max finished responses, in sequence order, to out; *n_out receives the count. */
+int abcore_serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out);
+
+/* Finish every submitted request, then stop serving. */
+int abcore_serve_stop(abcore_ctx *ctx);
+
+/* ---- introspection ----------------------------------------------------------------------- */
+
+/* Counters of the last compute call and the context's device memory. */
+int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
+
+/* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown. */
+int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
+
+/* Graph sizes of the loaded graph; any pointer may be NULL. */
+int abcore_graph_info(abcore_ctx *ctx, int32_t *nU, int32_t *nV, int64_t *m,
+                      int32_t *max_deg_u, int32_t *max_deg_v);
+
+/* Copy out the device CSR as stored: off[nU+nV+1] and adj[2m] over internal unified ids
+ * (U vertices 0..nU-1, V vertices nU..nU+nV-1, each layer ordered by non-increasing degree),
+ * and new2old[nU+nV], the caller's per-layer id of each internal vertex. */
+int abcore_export_csr(abcore_ctx *ctx, int64_t *off, int32_t *adj, int32_t *new2old, uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABCORE_H */

@@ -1,0 +1,187 @@
+"""Exact (alpha, beta)-core computation on bipartite graphs for one GB300 (sm_103a).
+
+``abi`` is the ctypes binding of include/abcore.h (same names). ``ABCore`` is a thin
+convenience wrapper that marshals torch tensors and numpy arrays into those calls; PyTorch
+provides device memory and streams only, every step runs in the library's CUDA kernels.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import abi
+from .buildlib import build, LIB
+
+__all__ = ["abi", "build", "LIB", "ABCore", "ABCoreError"]
+
+
+class ABCoreError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("abcore error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class ABCore:
+    """One library context on one CUDA device, ordered on one stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        abi.load_library()
+        self._h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        rc = abi.abcore_create(ctypes.byref(self._h), device, s)
+        if rc != 0:
+            raise ABCoreError(rc, "abcore_create failed")
+        self.device = device
+        self.nU = self.nV = self.m = 0
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise ABCoreError(rc, abi.abcore_last_error(self._h).decode(errors="replace"))
+        return rc
+
+    def close(self):
+        if self._h:
+            abi.abcore_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptr(x):
+        """(pointer, flags) of a contiguous torch tensor or numpy array."""
+        torch = _torch()
+        if isinstance(x, torch.Tensor):
+            assert x.is_contiguous()
+            return ctypes.c_void_p(x.data_ptr()), (abi.ABCORE_PTR_DEVICE if x.is_cuda else abi.ABCORE_PTR_HOST)
+        a = np.ascontiguousarray(x)
+        return ctypes.c_void_p(a.ctypes.data), abi.ABCORE_PTR_HOST
+
+    # -- loading ---------------------------------------------------------------------------
+    def load_edges(self, nU, nV, eu, ev):
+        torch = _torch()
+        if isinstance(eu, torch.Tensor):
+            eu = eu.to(torch.int32).contiguous()
+            ev = ev.to(torch.int32).contiguous()
+            assert eu.is_cuda == ev.is_cuda
+        else:
+            eu = np.ascontiguousarray(eu, dtype=np.int32)
+            ev = np.ascontiguousarray(ev, dtype=np.int32)
+        pu, fl = self._ptr(eu)
+        pv, _ = self._ptr(ev)
+        m = int(eu.numel() if isinstance(eu, torch.Tensor) else eu.size)
+        self._check(abi.abcore_load_edges(self._h, nU, nV, m, pu, pv, fl))
+        self.nU, self.nV, self.m = nU, nV, m
+
+    def load_csr(self, nU, nV, offU, adjU, offV=None, adjV=None, validate=False):
+        offU = np.ascontiguousarray(offU, dtype=np.int64)
+        adjU = np.ascontiguousarray(adjU, dtype=np.int32)
+        args = [self._ptr(offU)[0], self._ptr(adjU)[0]]
+        if offV is not None:
+            offV = np.ascontiguousarray(offV, dtype=np.int64)
+            adjV = np.ascontiguousarray(adjV, dtype=np.int32)
+            args += [self._ptr(offV)[0], self._ptr(adjV)[0]]
+        else:
+            args += [None, None]
+        fl = abi.ABCORE_PTR_HOST | (abi.ABCORE_VALIDATE if validate else 0)
+        self._check(abi.abcore_load_csr(self._h, nU, nV, *args, fl))
+        self.nU, self.nV, self.m = nU, nV, int(offU[nU])
+
+    # -- computation -----------------------------------------------------------------------
+    def compute(self, alpha, beta, out_u=None, out_v=None, asynchronous=False):
+        """Masks (uint8 0/1) of the (alpha, beta)-core; device tensors unless outputs are given."""
+        torch = _torch()
+        if out_u is None:
+            out_u = torch.empty(self.nU, dtype=torch.uint8, device="cuda:%d" % self.device)
+            out_v = torch.empty(self.nV, dtype=torch.uint8, device="cuda:%d" % self.device)
+        pu, fl = self._ptr(out_u)
+        pv, _ = self._ptr(out_v)
+        if asynchronous:
+            fl |= abi.ABCORE_ASYNC
+        self._check(abi.abcore_compute(self._h, int(alpha), int(beta), pu, pv, fl))
+        return out_u, out_v
+
+    def compute_batch(self, alphas, betas, out_u=None, out_v=None, asynchronous=False):
+        torch = _torch()
+        n = len(alphas)
+        a = np.ascontiguousarray(alphas, dtype=np.int32)
+        b = np.ascontiguousarray(betas, dtype=np.int32)
+        if out_u is None:
+            out_u = torch.empty((n, self.nU), dtype=torch.uint8, device="cuda:%d" % self.device)
+            out_v = torch.empty((n, self.nV), dtype=torch.uint8, device="cuda:%d" % self.device)
+        pu, fl = self._ptr(out_u)
+        pv, _ = self._ptr(out_v)
+        if asynchronous:
+            fl |= abi.ABCORE_ASYNC
+        self._check(abi.abcore_compute_batch(self._h, n, a.ctypes.data_as(ctypes.c_void_p),
+                                             b.ctypes.data_as(ctypes.c_void_p), pu, pv, fl))
+        return out_u, out_v
+
+    def sync(self):
+        self._check(abi.abcore_sync(self._h))
+
+    def query_edge(self, u, v, op, alpha, beta):
+        r = ctypes.c_uint8(0)
+        self._check(abi.abcore_query_edge(self._h, int(u), int(v), int(op), int(alpha), int(beta), ctypes.byref(r)))
+        return int(r.value)
+
+    # -- serving ---------------------------------------------------------------------------
+    def serve_start(self, targets, ring_slots=4096):
+        a = np.ascontiguousarray([t[0] for t in targets], dtype=np.int32)
+        b = np.ascontiguousarray([t[1] for t in targets], dtype=np.int32)
+        self._check(abi.abcore_serve_start(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                           b.ctypes.data_as(ctypes.c_void_p), len(targets), ring_slots))
+
+    def serve_submit(self, reqs):
+        """reqs: ctypes array of abi.abcore_req. Returns the sequence numbers, or None if busy."""
+        n = len(reqs)
+        seq = (ctypes.c_uint64 * max(n, 1))()
+        rc = abi.abcore_serve_submit(self._h, ctypes.cast(reqs, ctypes.c_void_p), n, ctypes.cast(seq, ctypes.c_void_p))
+        if rc == abi.ABCORE_EBUSY:
+            return None
+        self._check(rc)
+        return list(seq[:n])
+
+    def serve_poll(self, max_n=4096):
+        out = (abi.abcore_resp * max_n)()
+        got = ctypes.c_int32(0)
+        self._check(abi.abcore_serve_poll(self._h, ctypes.cast(out, ctypes.c_void_p), max_n, ctypes.byref(got)))
+        return out[:got.value]
+
+    def serve_stop(self):
+        self._check(abi.abcore_serve_stop(self._h))
+
+    # -- introspection ---------------------------------------------------------------------
+    def stats(self):
+        s = abi.abcore_stats()
+        self._check(abi.abcore_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def set_param(self, name, value):
+        self._check(abi.abcore_set_param(self._h, name.encode(), int(value)))
+
+    def graph_info(self):
+        nU, nV, du, dv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        m = ctypes.c_int64()
+        self._check(abi.abcore_graph_info(self._h, ctypes.byref(nU), ctypes.byref(nV), ctypes.byref(m),
+                                          ctypes.byref(du), ctypes.byref(dv)))
+        return dict(nU=nU.value, nV=nV.value, m=m.value, max_deg_u=du.value, max_deg_v=dv.value)
+
+    def export_csr(self):
+        n = self.nU + self.nV
+        off = np.zeros(n + 1, dtype=np.int64)
+        adj = np.zeros(max(2 * self.m, 1), dtype=np.int32)
+        n2o = np.zeros(max(n, 1), dtype=np.int32)
+        self._check(abi.abcore_export_csr(self._h, off.ctypes.data_as(ctypes.c_void_p),
+                                          adj.ctypes.data_as(ctypes.c_void_p),
+                                          n2o.ctypes.data_as(ctypes.c_void_p), abi.ABCORE_PTR_HOST))
+        return off, adj[: 2 * self.m], n2o[:n]

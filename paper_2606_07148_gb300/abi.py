@@ -1,0 +1,127 @@
+"""ctypes binding of the C ABI in include/abcore.h, with the same function names.
+
+Argument marshalling only: every computation happens in libabcore.so's CUDA kernels. Loading
+fails loudly if the library has not been built -- there is no fallback path.
+"""
+
+import ctypes
+import os
+
+from .buildlib import LIB
+
+ABCORE_OK = 0
+ABCORE_EINVAL = -1
+ABCORE_ENOTLOADED = -2
+ABCORE_ENOMEM = -3
+ABCORE_EEXIST = -4
+ABCORE_ENOENT = -5
+ABCORE_ECUDA = -6
+ABCORE_ETIMEDOUT = -7
+ABCORE_EBUSY = -8
+
+ABCORE_PTR_HOST = 0
+ABCORE_PTR_DEVICE = 1
+ABCORE_VALIDATE = 2
+ABCORE_ASYNC = 4
+
+ABCORE_INSERT = 0
+ABCORE_DELETE = 1
+
+EXPORTED = [
+    "abcore_create", "abcore_destroy", "abcore_last_error", "abcore_load_edges", "abcore_load_csr",
+    "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_query_edge",
+    "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
+    "abcore_get_stats", "abcore_set_param", "abcore_graph_info", "abcore_export_csr",
+]
+
+
+class abcore_stats(ctypes.Structure):
+    _fields_ = [
+        ("init_vertices", ctypes.c_int64), ("search_probes", ctypes.c_int64),
+        ("stream_entries", ctypes.c_int64), ("entries", ctypes.c_int64),
+        ("decrements", ctypes.c_int64), ("pushes", ctypes.c_int64), ("items", ctypes.c_int64),
+        ("candidates", ctypes.c_int64), ("steps", ctypes.c_int64), ("mode", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+        ("peak_device_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class abcore_req(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("u", ctypes.c_int32), ("v", ctypes.c_int32),
+                ("target", ctypes.c_int32), ("tag", ctypes.c_uint64)]
+
+
+class abcore_resp(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("in_core", ctypes.c_uint8), ("u_in", ctypes.c_uint8), ("v_in", ctypes.c_uint8),
+                ("pad", ctypes.c_uint8)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load_library(path: str = LIB):
+    """Load libabcore.so; raises if it is missing (build it with paper_2606_07148_gb300.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libabcore.so is not built (%s); run paper_2606_07148_gb300.build()" % path)
+    lib = ctypes.CDLL(path)
+    sig = {
+        "abcore_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
+        "abcore_destroy": ([_vp], ctypes.c_int),
+        "abcore_last_error": ([_vp], ctypes.c_char_p),
+        "abcore_load_edges": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_uint32],
+                              ctypes.c_int),
+        "abcore_load_csr": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
+        "abcore_compute": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
+        "abcore_compute_batch": ([_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
+        "abcore_sync": ([_vp], ctypes.c_int),
+        "abcore_query_edge": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
+        "abcore_serve_start": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "abcore_serve_submit": ([_vp, _vp, ctypes.c_int32, _vp], ctypes.c_int),
+        "abcore_serve_poll": ([_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "abcore_serve_stop": ([_vp], ctypes.c_int),
+        "abcore_get_stats": ([_vp, ctypes.POINTER(abcore_stats)], ctypes.c_int),
+        "abcore_set_param": ([_vp, ctypes.c_char_p, ctypes.c_int64], ctypes.c_int),
+        "abcore_graph_info": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "abcore_export_csr": ([_vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _fn(name):
+    def call(*args):
+        return getattr(load_library(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+abcore_create = _fn("abcore_create")
+abcore_destroy = _fn("abcore_destroy")
+abcore_last_error = _fn("abcore_last_error")
+abcore_load_edges = _fn("abcore_load_edges")
+abcore_load_csr = _fn("abcore_load_csr")
+abcore_compute = _fn("abcore_compute")
+abcore_compute_batch = _fn("abcore_compute_batch")
+abcore_sync = _fn("abcore_sync")
+abcore_query_edge = _fn("abcore_query_edge")
+abcore_serve_start = _fn("abcore_serve_start")
+abcore_serve_submit = _fn("abcore_serve_submit")
+abcore_serve_poll = _fn("abcore_serve_poll")
+abcore_serve_stop = _fn("abcore_serve_stop")
+abcore_get_stats = _fn("abcore_get_stats")
+abcore_set_param = _fn("abcore_set_param")
+abcore_graph_info = _fn("abcore_graph_info")
+abcore_export_csr = _fn("abcore_export_csr")

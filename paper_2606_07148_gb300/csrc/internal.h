@@ -1,0 +1,214 @@
+// Host-side internals of the abcore library: the context, the device-resident graph, the
+// per-query workspace, tuning parameters and the functions each translation unit provides.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/abcore.h"
+
+// Device-side control block of one peel (queue counters, error word, counters for stats).
+struct PeelCtl {
+    unsigned long long head;   // next queue slot to hand out
+    unsigned long long tail;   // queue slots reserved by pushers
+    unsigned long long done;   // queue slots fully processed
+    int err;                   // first error code (0 = none)
+    int pad;
+    unsigned long long st[8];  // stat counters, see ST_* below
+};
+enum {
+    ST_INIT = 0,     // candidate vertices initialised
+    ST_PROBES = 1,   // adjacency words read by the in-candidate degree search
+    ST_STREAM = 2,   // adjacency entries streamed from initial violators
+    ST_ENTRIES = 3,  // adjacency entries read by the cascade
+    ST_DECS = 4,     // atomic decrements
+    ST_PUSHES = 5,   // vertices queued
+    ST_ITEMS = 6,    // cascade work items processed
+    ST_STEPS = 7,    // chain steps (batch)
+};
+
+// Everything a peel kernel needs, passed by value.
+struct PeelArgs {
+    const int64_t *off;      // [n+1] row offsets, internal unified ids
+    const int32_t *adj;      // [2m] neighbours, each row ascending
+    int2 *cp;                // [n] {count of live candidate neighbours, row prefix length}
+    unsigned long long *q;   // [qcap] work queue of (vertex << 32 | chunk); ~0 = empty slot
+    long long qcap;
+    PeelCtl *ctl;
+    int32_t nU, nV;
+    int32_t pU, pV;          // candidate prefixes: U [0,pU), V [nU, nU+pV)
+    int32_t thrU, thrV;      // alpha, beta
+    int32_t chunk;           // adjacency entries per work item
+    int32_t grab_div;        // queue items per grab = clamp(available / grab_div, 1, 32)
+    int32_t searchU;         // 1: U counts by searching U rows; 0: by streaming V violators
+    int32_t searchV;         // 1: V counts by searching V rows; 0: by streaming U violators
+    unsigned long long timeout_ns;
+    // mask emission
+    const int32_t *old2new;  // [n] caller id (layer base + id) -> internal id
+    const int32_t *new2old;  // [n] internal id -> caller per-layer id
+    uint8_t *mask_u, *mask_v;
+    int32_t emit;            // 0 none, 1 gather over all vertices, 2 scatter of live candidates
+    int32_t pad;
+};
+
+struct Params {
+    int chunk = 1024;
+    int grab_div = 0;          // 0 = automatic (resident warps / 8)
+    int threads = 256;
+    int blocks_per_sm = 0;     // 0 = occupancy calculator
+    int mode = -1;             // -1 auto; else bit 0 searchU, bit 1 searchV
+    long long timeout_ms = 4000;
+    int emit_scatter_max_pct = 5;  // scatter masks when |P| <= this % of n
+    double probe_bytes = 64.0;     // cost model: bytes per search probe
+    int batch_groups = 0;      // 0 = one group per chain
+    int debug_stall_slots = 0; // test hook: queue slots reserved but never written
+};
+
+struct Graph {
+    bool loaded = false;
+    int32_t nU = 0, nV = 0;
+    int64_t m = 0;
+    int64_t *off = nullptr;      // [n+1]
+    int32_t *adj = nullptr;      // [2m]
+    int32_t *new2old = nullptr;  // [n]
+    int32_t *old2new = nullptr;  // [n]
+    int32_t maxdegU = 0, maxdegV = 0;
+    // host tables indexed by degree threshold t (0..maxdeg+1):
+    // cnt_ge[t] = #vertices with degree >= t, edges_ge[t] = sum of their degrees
+    std::vector<int64_t> cntU_ge, edgesU_ge, cntV_ge, edgesV_ge;
+    int64_t n() const { return (int64_t)nU + nV; }
+};
+
+constexpr int CTL_RING = 64;  // peels that may be in flight (ABCORE_ASYNC) before a forced wait
+
+struct PeelWork {
+    int64_t n = 0, qcap = 0;
+    int2 *cp = nullptr;
+    unsigned long long *q = nullptr;
+    PeelCtl *ctl = nullptr;        // [CTL_RING] device control blocks
+    PeelCtl *ctl_host = nullptr;   // [CTL_RING] pinned readback
+    bool pending[CTL_RING] = {};
+    int next = 0, last = -1;
+    uint8_t *stage = nullptr;      // [n] staging for host-pointer masks
+    bool q_dirty = false;          // queue not known to be all-empty
+};
+
+struct BatchState;
+struct ServeState;
+
+struct abcore_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string err;
+    Graph g;
+    PeelWork w;
+    Params prm;
+    abcore_stats stats{};
+    int64_t dev_bytes = 0, peak_bytes = 0;
+    int cascade_blocks = 0;
+    BatchState *batch = nullptr;
+    ServeState *serve = nullptr;
+    bool pending_async = false;
+
+    int fail(int code, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char *what) {
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(ABCORE_ENOMEM, "%s: out of device memory", what);
+        }
+        return fail(ABCORE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    template <class T>
+    int alloc(T **p, size_t count, const char *what) {
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        *p = (T *)q;
+        dev_bytes += (int64_t)bytes;
+        if (dev_bytes > peak_bytes) peak_bytes = dev_bytes;
+        alloc_sizes.push_back({q, (int64_t)bytes});
+        return ABCORE_OK;
+    }
+    template <class T>
+    void release(T *&p) {
+        if (!p) return;
+        for (size_t i = 0; i < alloc_sizes.size(); ++i)
+            if (alloc_sizes[i].first == (void *)p) {
+                dev_bytes -= alloc_sizes[i].second;
+                alloc_sizes[i] = alloc_sizes.back();
+                alloc_sizes.pop_back();
+                break;
+            }
+        cudaFree((void *)p);
+        p = nullptr;
+    }
+    std::vector<std::pair<void *, int64_t>> alloc_sizes;
+};
+
+#define ABC_CU(call)                                              \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call);  \
+    } while (0)
+
+#define ABC_TRY(call)                  \
+    do {                               \
+        int rc_ = (call);              \
+        if (rc_ != ABCORE_OK) return rc_; \
+    } while (0)
+
+// build.cu -- device CSR builder
+int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64_t m,
+                                  const int32_t *d_eu, const int32_t *d_ev);
+int expand_csr_to_edges(abcore_ctx *ctx, int32_t nU, const int64_t *d_off, const int32_t *d_adj,
+                        int64_t m, int32_t *d_eu);
+int check_csr_offsets(abcore_ctx *ctx, int32_t nrows, const int64_t *d_off, int64_t m);
+int compare_edge_sets(abcore_ctx *ctx, int32_t nV, int64_t m, const int32_t *eu1, const int32_t *ev1,
+                      const int32_t *eu2, const int32_t *ev2);
+void free_graph(abcore_ctx *ctx);
+
+// peel.cu -- single (alpha, beta)-core
+int peel_prepare(abcore_ctx *ctx);
+int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
+                 bool sync_and_check);
+int peel_finish(abcore_ctx *ctx);
+void free_peel(abcore_ctx *ctx);
+int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, int32_t pV);
+int cascade_grid(abcore_ctx *ctx);
+
+// batch.cu
+int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
+                  uint8_t *d_masks_u, uint8_t *d_masks_v, bool sync_and_check);
+void free_batch(abcore_ctx *ctx);
+
+// serve.cu
+int query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta,
+               uint8_t *in_core);
+int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t nt, int32_t slots);
+int serve_submit(abcore_ctx *ctx, const abcore_req *reqs, int32_t n, uint64_t *seq_out);
+int serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out);
+int serve_stop(abcore_ctx *ctx);
+void free_serve(abcore_ctx *ctx);
+
+static inline int64_t cnt_ge(const std::vector<int64_t> &t, int32_t thr) {
+    if (thr <= 0) return t.empty() ? 0 : t[0];
+    if ((size_t)thr >= t.size()) return 0;
+    return t[thr];
+}

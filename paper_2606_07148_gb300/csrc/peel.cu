@@ -1,0 +1,389 @@
+// Single (alpha, beta)-core peel (Definition 1; Algorithm 1, GCC).
+//
+// Layout fact used throughout: each layer is numbered by non-increasing degree, so the
+// vertices that meet their bound on full degree -- the only ones that can be in the core --
+// are the prefixes P_U = [0, pU) and P_V = [nU, nU + pV). Every other vertex violates at once
+// (the scan phase of Algorithm 1) and is never looked at individually.
+//
+// Three launches:
+//  1. k_init: for each candidate x, its count of live candidate neighbours. Per layer, either
+//     (search) a binary search in x's sorted row for the candidate boundary of the other layer,
+//     which equals the count left after removing all initial violators; or (stream) the full
+//     degree, corrected by step 2. Candidates already below their bound are queued.
+//  2. k_stream (only for layers counted by full degree): the rows of the initial violators of
+//     the other layer form one contiguous slice of adj; it is streamed with 16-byte loads and
+//     every entry that hits a candidate decrements it (the paper's first peel round).
+//  3. k_cascade: the work-queue cascade (peel_core.cuh), then each warp writes its share of
+//     the masks in the caller's ids.
+#include <algorithm>
+#include <cmath>
+
+#include "device.cuh"
+#include "internal.h"
+#include "peel_core.cuh"
+
+namespace {
+
+using abc::LaneStats;
+using abc::WarpSmem;
+
+constexpr int INIT_THREADS = 256;
+constexpr int STREAM_THREADS = 256;
+
+__global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
+    const int64_t P = (int64_t)a.pU + a.pV;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    LaneStats ls;
+    unsigned long long probes = 0, inits = 0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < P; b += stride) {
+        const int64_t i = b + threadIdx.x;
+        bool viol = false;
+        int32_t x = 0;
+        int nch = 0;
+        if (i < P) {
+            x = i < a.pU ? (int32_t)i : (int32_t)(a.nU + (i - a.pU));
+            const bool upper = x < a.nU;
+            const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
+            int len;
+            if (upper ? a.searchU : a.searchV) {
+                const int32_t bound = upper ? a.nU + a.pV : a.pU;
+                if (e == s) {
+                    len = 0;
+                } else if (__ldg(&a.adj[e - 1]) < bound) {
+                    len = (int)(e - s);
+                    probes++;
+                } else {
+                    int64_t lo = s, hi = e - 1;  // adj[hi] >= bound
+                    probes++;
+                    while (lo < hi) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        probes++;
+                        if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    len = (int)(lo - s);
+                }
+            } else {
+                len = (int)(e - s);
+            }
+            a.cp[x] = make_int2(len, len);
+            inits++;
+            const int32_t thr = upper ? a.thrU : a.thrV;
+            viol = len < thr;
+            nch = abc::chunks_of(len, a.chunk);
+        }
+        abc::warp_push(a, viol, x, nch, ls);
+    }
+    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)inits);
+    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)probes);
+    unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
+    if ((threadIdx.x & 31) == 0) {
+        if (v0) atomicAdd(&a.ctl->st[ST_INIT], v0);
+        if (v1) atomicAdd(&a.ctl->st[ST_PROBES], v1);
+        if (v2) atomicAdd(&a.ctl->st[ST_PUSHES], v2);
+    }
+}
+
+// Stream adjacency slices of initial violators; entries landing on candidates decrement them.
+// Slice A = [sa, ea) holds V rows (entries are U ids), slice B = [sb, eb) holds U rows.
+__device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool from_upper, bool valid,
+                                             LaneStats &ls) {
+    bool push = false;
+    int nch = 0;
+    if (valid) {
+        int32_t thr;
+        if (abc::cand_of(a, y, from_upper, thr) && thr > 0) {
+            const int old = atomicSub(&a.cp[y].x, 1);
+            ls.decs++;
+            if (old == thr) {
+                push = true;
+                nch = abc::chunks_of(abc::row_len_of(a, y), a.chunk);
+            }
+        }
+    }
+    abc::warp_push(a, push, y, nch, ls);
+}
+
+__global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t sa, int64_t ea, int64_t sb,
+                                                           int64_t eb) {
+    LaneStats ls;
+    unsigned long long ents = 0;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int64_t s = sl == 0 ? sa : sb, e = sl == 0 ? ea : eb;
+        if (e <= s) continue;
+        const bool from_upper = sl == 1;
+        const int64_t a0 = min((s + 3) & ~(int64_t)3, e);
+        const int64_t a1 = max(e & ~(int64_t)3, a0);
+        // unaligned head and tail, scalar
+        {
+            const int64_t nh = (a0 - s) + (e - a1);
+            for (int64_t b = 0; b < nh; b += nthreads) {
+                const int64_t i = b + tid;
+                const bool valid = i < nh;
+                int32_t y = 0;
+                if (valid) {
+                    const int64_t pos = i < (a0 - s) ? s + i : a1 + (i - (a0 - s));
+                    y = __ldg(&a.adj[pos]);
+                    ents++;
+                }
+                stream_entry(a, y, from_upper, valid, ls);
+            }
+        }
+        const int64_t nv = (a1 - a0) >> 2;
+        const int4 *v4 = reinterpret_cast<const int4 *>(a.adj + a0);
+        for (int64_t b = 0; b < nv; b += nthreads) {
+            const int64_t i = b + tid;
+            const bool valid = i < nv;
+            int4 q = make_int4(0, 0, 0, 0);
+            if (valid) {
+                q = __ldg(&v4[i]);
+                ents += 4;
+            }
+            stream_entry(a, q.x, from_upper, valid, ls);
+            stream_entry(a, q.y, from_upper, valid, ls);
+            stream_entry(a, q.z, from_upper, valid, ls);
+            stream_entry(a, q.w, from_upper, valid, ls);
+        }
+    }
+    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)ents);
+    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.decs);
+    unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
+    if ((threadIdx.x & 31) == 0) {
+        if (v0) atomicAdd(&a.ctl->st[ST_STREAM], v0);
+        if (v1) atomicAdd(&a.ctl->st[ST_DECS], v1);
+        if (v2) atomicAdd(&a.ctl->st[ST_PUSHES], v2);
+    }
+}
+
+__device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
+    if (x < a.nU) return x < a.pU && __ldcg(&a.cp[x].x) >= a.thrU;
+    return x < a.nU + a.pV && __ldcg(&a.cp[x].x) >= a.thrV;
+}
+
+__global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
+    __shared__ WarpSmem smem[256 / 32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    LaneStats ls;
+    const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div);
+    abc::flush_stats(a, ls);
+    if (!ok || a.emit == 0) return;
+    const int64_t n = (int64_t)a.nU + a.nV;
+    if (a.emit == 1) {
+        for (int64_t i = gw * 32 + lane; i < n; i += nw * 32) {
+            const int32_t x = __ldg(&a.old2new[i]);
+            const uint8_t v = alive_of(a, x) ? 1 : 0;
+            if (i < a.nU) a.mask_u[i] = v;
+            else a.mask_v[i - a.nU] = v;
+        }
+    } else {
+        const int64_t P = (int64_t)a.pU + a.pV;
+        for (int64_t p = gw * 32 + lane; p < P; p += nw * 32) {
+            const int32_t x = p < a.pU ? (int32_t)p : (int32_t)(a.nU + (p - a.pU));
+            if (alive_of(a, x)) {
+                const int32_t o = __ldg(&a.new2old[x]);
+                if (x < a.nU) a.mask_u[o] = 1;
+                else a.mask_v[o] = 1;
+            }
+        }
+    }
+}
+
+// Test hook: reserve queue slots that nothing will fill, so the consumers' bounded wait expires.
+__global__ void k_stall(PeelCtl *ctl, long long qcap, int n) {
+    if (ctl->tail + (unsigned long long)n <= (unsigned long long)qcap) atomicAdd(&ctl->tail, (unsigned long long)n);
+}
+
+}  // namespace
+
+int cascade_grid(abcore_ctx *ctx) {
+    if (ctx->cascade_blocks > 0) return ctx->cascade_blocks;
+    int per_sm = ctx->prm.blocks_per_sm;
+    if (per_sm <= 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cascade, 256, 0);
+        if (per_sm <= 0) per_sm = 1;
+    }
+    ctx->cascade_blocks = per_sm * ctx->num_sms;
+    return ctx->cascade_blocks;
+}
+
+int peel_prepare(abcore_ctx *ctx) {
+    PeelWork &w = ctx->w;
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024;
+    if (w.n == n && w.qcap >= qcap && w.cp) return ABCORE_OK;
+    free_peel(ctx);
+    ABC_TRY(ctx->alloc(&w.cp, (size_t)std::max<int64_t>(n, 1), "peel counts"));
+    ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
+    ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
+    ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
+    ABC_CU(cudaMallocHost(&w.ctl_host, sizeof(PeelCtl) * CTL_RING));
+    for (int i = 0; i < CTL_RING; ++i) w.pending[i] = false;
+    w.next = 0;
+    w.last = -1;
+    ABC_CU(cudaMemsetAsync(w.q, 0xff, sizeof(unsigned long long) * (size_t)qcap, ctx->stream));
+    w.n = n;
+    w.qcap = qcap;
+    w.q_dirty = false;
+    return ABCORE_OK;
+}
+
+void free_peel(abcore_ctx *ctx) {
+    PeelWork &w = ctx->w;
+    ctx->release(w.cp);
+    ctx->release(w.q);
+    ctx->release(w.ctl);
+    ctx->release(w.stage);
+    if (w.ctl_host) cudaFreeHost(w.ctl_host);
+    w.ctl_host = nullptr;
+    for (int i = 0; i < CTL_RING; ++i) w.pending[i] = false;
+    w.last = -1;
+    w.n = w.qcap = 0;
+}
+
+// Cost model: per layer, count by searching the candidates' rows, or by streaming the rows of
+// the other layer's initial violators? Both reach the same counts; pick the cheaper in bytes.
+int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, int32_t pV) {
+    const Graph &g = ctx->g;
+    if (ctx->prm.mode >= 0) return ctx->prm.mode & 3;
+    const double m = (double)std::max<int64_t>(g.m, 1);
+    const double eU = (double)cnt_ge(g.edgesU_ge, alpha);  // sum of degrees of U candidates
+    const double eV = (double)cnt_ge(g.edgesV_ge, beta);
+    const double fU = eU / m, fV = eV / m;
+    auto search_cost = [&](int64_t p, double edges) {
+        if (p == 0) return 0.0;
+        const double avg = edges / (double)p;
+        return (double)p * (16.0 + ctx->prm.probe_bytes * (1.0 + std::log2(std::max(avg, 2.0))));
+    };
+    // U counts: search U rows, or stream the rows of V violators (m - eV entries)
+    const double sU = search_cost(pU, eU), tU = (m - eV) * (4.0 + 8.0 * fU) + 12.0 * pU;
+    const double sV = search_cost(pV, eV), tV = (m - eU) * (4.0 + 8.0 * fV) + 12.0 * pV;
+    return (sU <= tU ? 1 : 0) | (sV <= tV ? 2 : 0);
+}
+
+int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
+                 bool sync_and_check) {
+    const Graph &g = ctx->g;
+    PeelWork &w = ctx->w;
+    ABC_TRY(peel_prepare(ctx));
+    const int32_t nU = g.nU, nV = g.nV;
+    const int64_t n = g.n();
+    const int32_t pU = (int32_t)cnt_ge(g.cntU_ge, alpha);
+    const int32_t pV = (int32_t)cnt_ge(g.cntV_ge, beta);
+    const int64_t P = (int64_t)pU + pV;
+    const int mode = pick_mode(ctx, alpha, beta, pU, pV);
+
+    const int slot = w.next;
+    if (w.pending[slot]) ABC_TRY(peel_finish(ctx));  // ring wrapped: wait for the oldest peels
+    w.next = (w.next + 1) % CTL_RING;
+    PeelCtl *ctl = w.ctl + slot;
+
+    PeelArgs a{};
+    a.off = g.off;
+    a.adj = g.adj;
+    a.cp = w.cp;
+    a.q = w.q;
+    a.qcap = w.qcap;
+    a.ctl = ctl;
+    a.nU = nU;
+    a.nV = nV;
+    a.pU = pU;
+    a.pV = pV;
+    a.thrU = alpha;
+    a.thrV = beta;
+    a.chunk = std::max(ctx->prm.chunk, 32);
+    const int blocks = cascade_grid(ctx);
+    a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
+    a.searchU = mode & 1;
+    a.searchV = (mode >> 1) & 1;
+    a.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
+    a.old2new = g.old2new;
+    a.new2old = g.new2old;
+    a.mask_u = d_mask_u;
+    a.mask_v = d_mask_v;
+    const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
+    a.emit = scatter ? 2 : 1;
+
+    if (w.q_dirty) {
+        ABC_CU(cudaMemsetAsync(w.q, 0xff, sizeof(unsigned long long) * (size_t)w.qcap, ctx->stream));
+        w.q_dirty = false;
+    }
+    ABC_CU(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), ctx->stream));
+    if (scatter) {
+        if (nU) ABC_CU(cudaMemsetAsync(d_mask_u, 0, (size_t)nU, ctx->stream));
+        if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
+    }
+    if (P > 0) {
+        const int64_t gi = std::min<int64_t>((P + INIT_THREADS - 1) / INIT_THREADS, (int64_t)ctx->num_sms * 32);
+        k_init<<<(unsigned)std::max<int64_t>(gi, 1), INIT_THREADS, 0, ctx->stream>>>(a);
+        // Rows of the initial violators are contiguous: U violators [pU, nU) own
+        // adj[off[pU], off[nU]) = [edgesU_ge(alpha), m), V violators [nU+pV, n) own
+        // adj[m + edgesV_ge(beta), 2m). Slice A (V rows) feeds U counts, slice B (U rows) V counts.
+        int64_t sa = 0, ea = 0, sb = 0, eb = 0;
+        if (!a.searchU && pU > 0) {
+            sa = g.m + cnt_ge(g.edgesV_ge, beta);
+            ea = 2 * g.m;
+        }
+        if (!a.searchV && pV > 0) {
+            sb = cnt_ge(g.edgesU_ge, alpha);
+            eb = g.m;
+        }
+        if (ea > sa || eb > sb) {
+            const int64_t work = ((ea - sa) + (eb - sb)) / 4 + 1;
+            const int64_t gs = std::min<int64_t>((work + STREAM_THREADS - 1) / STREAM_THREADS,
+                                                 (int64_t)ctx->num_sms * 16);
+            k_stream<<<(unsigned)std::max<int64_t>(gs, 1), STREAM_THREADS, 0, ctx->stream>>>(a, sa, ea, sb, eb);
+        }
+    }
+    if (ctx->prm.debug_stall_slots > 0) k_stall<<<1, 1, 0, ctx->stream>>>(ctl, w.qcap, ctx->prm.debug_stall_slots);
+    k_cascade<<<blocks, 256, 0, ctx->stream>>>(a);
+    ABC_CU(cudaGetLastError());
+    ABC_CU(cudaMemcpyAsync(w.ctl_host + slot, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    w.pending[slot] = true;
+    w.last = slot;
+    ctx->stats.candidates = P;
+    ctx->stats.mode = mode;
+    ctx->stats.grid_blocks = blocks;
+    ctx->pending_async = true;
+    if (sync_and_check) return peel_finish(ctx);
+    return ABCORE_OK;
+}
+
+// Wait for every peel in flight and turn their device status into a return code; the stats
+// describe the most recent one.
+int peel_finish(abcore_ctx *ctx) {
+    if (!ctx->pending_async) return ABCORE_OK;
+    ctx->pending_async = false;
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    PeelWork &w = ctx->w;
+    int first_err = 0;
+    for (int i = 0; i < CTL_RING; ++i) {
+        if (!w.pending[i]) continue;
+        w.pending[i] = false;
+        if (w.ctl_host[i].err != 0 && first_err == 0) first_err = w.ctl_host[i].err;
+    }
+    if (w.last >= 0) {
+        const PeelCtl &c = w.ctl_host[w.last];
+        abcore_stats &s = ctx->stats;
+        s.init_vertices = (int64_t)c.st[ST_INIT];
+        s.search_probes = (int64_t)c.st[ST_PROBES];
+        s.stream_entries = (int64_t)c.st[ST_STREAM];
+        s.entries = (int64_t)c.st[ST_ENTRIES];
+        s.decrements = (int64_t)c.st[ST_DECS];
+        s.pushes = (int64_t)c.st[ST_PUSHES];
+        s.items = (int64_t)c.st[ST_ITEMS];
+        s.steps = (int64_t)c.st[ST_STEPS];
+    }
+    if (first_err != 0) {
+        w.q_dirty = true;
+        if (first_err == ABCORE_ETIMEDOUT)
+            return ctx->fail(ABCORE_ETIMEDOUT, "peel: a bounded device wait expired (limit %lld ms)",
+                             (long long)ctx->prm.timeout_ms);
+        return ctx->fail(first_err, "peel: device reported error %d", first_err);
+    }
+    return ABCORE_OK;
+}

@@ -1,0 +1,237 @@
+"""GPU parity of the device CSR builder and the single (alpha, beta)-core peel against the oracle.
+
+Masks are integer results, so the bar is bit-exact equality with the oracle on the same seeded
+input. Every call goes through the C ABI (paper_2606_07148_gb300.abi via the ABCore wrapper).
+"""
+
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2606_07148_gb300 import ABCore, ABCoreError, abi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_07148_gb300.buildlib import build
+    build()
+
+
+def _np(t):
+    return t.cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
+
+
+def _check_pairs(core, nU, nV, eu, ev, pairs, off=None, adj=None):
+    if off is None:
+        off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    for a, b in pairs:
+        mu, mv = core.compute(a, b)
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        gu, gv = _np(mu), _np(mv)
+        assert np.array_equal(gu, wu) and np.array_equal(gv, wv), \
+            "(%d,%d): U diff %d, V diff %d" % (a, b, int((gu != wu).sum()), int((gv != wv).sum()))
+
+
+# ------------------------------------------------------------------------------------------
+# device CSR builder
+# ------------------------------------------------------------------------------------------
+def _check_export(core, nU, nV, eu, ev):
+    off, adj, n2o = core.export_csr()
+    o_off, o_adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    n = nU + nV
+    assert off[0] == 0 and off[n] == 2 * len(_np(eu))
+    assert sorted(n2o[:nU].tolist()) == list(range(nU))
+    assert sorted(n2o[nU:].tolist()) == list(range(nV))
+    deg = np.diff(off)
+    assert np.all(np.diff(deg[:nU]) <= 0) and np.all(np.diff(deg[nU:]) <= 0)
+    old_unified = np.concatenate([n2o[:nU], n2o[nU:] + nU]).astype(np.int64)
+    for x in range(n):
+        row = adj[off[x]:off[x + 1]]
+        assert np.all(np.diff(row) > 0)
+        if x < nU:
+            assert np.all((row >= nU) & (row < n))
+        else:
+            assert np.all((row >= 0) & (row < nU))
+        ox = old_unified[x]
+        want = o_adj[o_off[ox]:o_off[ox + 1]]
+        assert np.array_equal(np.sort(old_unified[row]), want)
+
+
+def test_csr_builder_matches_oracle():
+    core = ABCore(0)
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    _check_export(core, nU, nV, eu, ev)
+    rng = random.Random(3)
+    for _ in range(6):
+        nU, nV = rng.randint(1, 300), rng.randint(1, 300)
+        m = rng.randint(0, min(nU * nV, 3000))
+        eu, ev = synth.chung_lu_edges(nU, nV, m, 2.2, 2.2, rng.randint(0, 999)) if m else (
+            torch.zeros(0, dtype=torch.int32), torch.zeros(0, dtype=torch.int32))
+        core.load_edges(nU, nV, eu, ev)  # host pointers
+        _check_export(core, nU, nV, eu, ev)
+    core.close()
+
+
+def test_csr_builder_rejects_bad_input():
+    core = ABCore(0)
+    with pytest.raises(ABCoreError) as e:
+        core.load_edges(3, 3, np.array([0, 1, 0]), np.array([1, 2, 1]))
+    assert e.value.code == abi.ABCORE_EEXIST
+    with pytest.raises(ABCoreError) as e:
+        core.load_edges(3, 3, np.array([0, 3]), np.array([1, 2]))
+    assert e.value.code == abi.ABCORE_EINVAL
+    with pytest.raises(ABCoreError) as e:
+        core.load_edges(3, 3, np.array([0, 1]), np.array([-1, 2]))
+    assert e.value.code == abi.ABCORE_EINVAL
+    with pytest.raises(ABCoreError) as e:
+        core.compute(1, 1)
+    assert e.value.code == abi.ABCORE_ENOTLOADED
+    core.load_edges(3, 3, np.array([0, 1]), np.array([1, 2]))
+    with pytest.raises(ABCoreError) as e:
+        core.compute(-1, 1)
+    assert e.value.code == abi.ABCORE_EINVAL
+    core.close()
+
+
+def test_load_csr_and_validation():
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    m = len(eu)
+    offU, adjU = off[:nU + 1], adj[:m] - nU
+    offV, adjV = off[nU:] - m, adj[m:]
+    core = ABCore(0)
+    core.load_csr(nU, nV, offU, adjU, offV, adjV, validate=True)
+    _check_pairs(core, nU, nV, eu, ev, [(2, 3), (4, 4)], off, adj)
+    bad = adjV.copy()
+    bad[0], bad[-1] = bad[-1], bad[0]
+    if not np.array_equal(bad, adjV):
+        with pytest.raises(ABCoreError) as e:
+            core.load_csr(nU, nV, offU, adjU, offV, bad, validate=True)
+        assert e.value.code == abi.ABCORE_EINVAL
+    bad_off = offU.copy()
+    bad_off[1], bad_off[2] = bad_off[2] + 5, bad_off[1]
+    with pytest.raises(ABCoreError):
+        core.load_csr(nU, nV, bad_off, adjU)
+    core.close()
+
+
+# ------------------------------------------------------------------------------------------
+# the peel
+# ------------------------------------------------------------------------------------------
+PAIRS_SMALL = [(a, b) for a in (0, 1, 2, 3, 5, 8, 13, 40, 250) for b in (0, 1, 2, 3, 4, 7, 21, 300)]
+
+
+@pytest.mark.parametrize("mode", [-1, 0, 1, 2, 3])
+@pytest.mark.parametrize("chunk", [32, 1024])
+def test_peel_small_graph_all_modes(mode, chunk):
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    core = ABCore(0)
+    core.set_param("mode", mode)
+    core.set_param("chunk", chunk)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    _check_pairs(core, nU, nV, eu, ev, PAIRS_SMALL)
+    core.close()
+
+
+def test_peel_tiny_random_graphs():
+    rng = random.Random(17)
+    core = ABCore(0)
+    for _ in range(40):
+        nU, nV = rng.randint(1, 12), rng.randint(1, 12)
+        edges = [(u, v) for u in range(nU) for v in range(nV) if rng.random() < rng.uniform(0.1, 0.9)]
+        eu = np.array([e[0] for e in edges], dtype=np.int32)
+        ev = np.array([e[1] for e in edges], dtype=np.int32)
+        core.load_edges(nU, nV, eu, ev)
+        core.set_param("mode", rng.randint(-1, 3))
+        _check_pairs(core, nU, nV, eu, ev, [(rng.randint(0, 6), rng.randint(0, 6)) for _ in range(6)])
+    core.close()
+
+
+def test_peel_edge_cases():
+    core = ABCore(0)
+    # no edges: a vertex survives only if its layer's threshold is 0
+    core.load_edges(5, 4, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    for a, b in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        mu, mv = core.compute(a, b)
+        assert _np(mu).tolist() == [int(a == 0)] * 5 and _np(mv).tolist() == [int(b == 0)] * 4
+    # empty layers
+    core.load_edges(0, 3, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    mu, mv = core.compute(0, 0)
+    assert _np(mv).tolist() == [1, 1, 1]
+    # complete bipartite K_{4,6} with isolated extras
+    eu = np.repeat(np.arange(4), 6).astype(np.int32)
+    ev = np.tile(np.arange(6), 4).astype(np.int32)
+    core.load_edges(7, 9, eu, ev)
+    _check_pairs(core, 7, 9, eu, ev, [(a, b) for a in range(0, 8) for b in range(0, 6)] + [(10**6, 1), (1, 10**6)])
+    core.close()
+
+
+def test_host_and_device_pointers_and_async_agree():
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.numpy(), ev.numpy())
+    pairs = [(2, 3), (3, 3), (1, 7), (6, 2), (9, 9)]
+    outs = []
+    for a, b in pairs:
+        hu = np.zeros(nU, np.uint8)
+        hv = np.zeros(nV, np.uint8)
+        core.compute(a, b, hu, hv)
+        du = torch.empty(nU, dtype=torch.uint8, device="cuda")
+        dv = torch.empty(nV, dtype=torch.uint8, device="cuda")
+        core.compute(a, b, du, dv, asynchronous=True)
+        outs.append((du, dv, hu, hv))
+    core.sync()
+    for (a, b), (du, dv, hu, hv) in zip(pairs, outs):
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        assert np.array_equal(hu, wu) and np.array_equal(hv, wv)
+        assert np.array_equal(_np(du), wu) and np.array_equal(_np(dv), wv)
+    core.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    """A queue slot that nothing fills makes the cascade's bounded wait expire: the call returns
+    ABCORE_ETIMEDOUT, and the next call on the same context is correct."""
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.set_param("timeout_ms", 50)
+    core.set_param("debug_stall_slots", 1)
+    with pytest.raises(ABCoreError) as e:
+        core.compute(2, 3)
+    assert e.value.code == abi.ABCORE_ETIMEDOUT
+    core.set_param("debug_stall_slots", 0)
+    core.set_param("timeout_ms", 4000)
+    _check_pairs(core, nU, nV, eu, ev, [(2, 3), (5, 5)])
+    core.close()
+
+
+def test_peel_mid_size_power_law():
+    nU, nV, m = 400_000, 200_000, 8_000_000
+    eu, ev = synth.chung_lu_edges(nU, nV, m, 2.1, 2.4, seed=11, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    pairs = [(2, 2), (5, 3), (10, 10), (20, 5), (50, 50), (1, 100), (100, 1), (0, 30)]
+    for mode in (-1, 0, 3):
+        core.set_param("mode", mode)
+        _check_pairs(core, nU, nV, eu, ev, pairs, off, adj)
+    core.close()
+
+
+def test_peel_full_size_4Mx2M_80M():
+    """The five single peels at full size, each compared byte for byte with the oracle."""
+    spec = synth.WORKLOADS["peel-4Mx2M-80M"]
+    nU, nV, eu, ev = synth.make_graph(spec, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    _check_pairs(core, nU, nV, eu, ev, spec["pairs"], off, adj)
+    core.close()
