@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Benchmark of the (alpha, beta)-core library on one GB300 (or N replicas under torchrun).
+
+Default workload: the plain single peels on a seeded Chung-Lu graph with |U| = 4M, |V| = 2M and
+80M edges (exponents 2.1 / 2.4, seed 1); one step = the five (alpha, beta) queries
+(2,2) (5,3) (10,10) (20,5) (50,50), each its own abcore_compute call, on the resident CSR (the
+one-time CSR build is timed separately and reported in config). The metric is peel GTEPS:
+input edges per second per peel, summed over the queries of a step and over all ranks.
+
+Other workloads (--workload): "billion-100Mx50M-1500M" (the (64,64) single peel on the 1.5B-edge
+graph), "batch-20Mx10M-500M" / "billion-batch" (batched cores/s), "serve-10Mx5M-200M"
+(edge-query latency). --impl reference times the CPU oracle on the same workload.
+
+One JSON line is printed by rank 0.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+PEAK_FALLBACK_GBS = 6800.0
+
+
+# ------------------------------------------------------------------------------------------
+# environment: ranks, peaks, clocks
+# ------------------------------------------------------------------------------------------
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "20", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.05)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 10:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(rows)}
+        sm = []
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                out["sm_max_mhz"] = float(r[3])
+            except ValueError:
+                pass
+            for name, col in (("hw_slowdown", 6), ("hw_thermal_slowdown", 7), ("sw_thermal_slowdown", 8),
+                              ("sw_power_cap", 9)):
+                if r[col].lower().startswith("active") and name not in out["reasons"]:
+                    out["reasons"].append(name)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+        return out
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ------------------------------------------------------------------------------------------
+# roofline bookkeeping (per-unit algorithmic bytes; the figures are documented in the design doc)
+# ------------------------------------------------------------------------------------------
+KERNEL_NAMES = {0: "k_init", 1: "k_stream", 2: "k_cascade", 3: "k_batch", 4: "k_serve"}
+
+
+def algorithmic_bytes(st):
+    """Bytes each kernel kind must move, from the library's accumulated counters."""
+    b = {}
+    # init: per candidate 8 B of offsets (consecutive rows share them) + 8 B count/prefix write;
+    # 4 B per word probed by the boundary search
+    b[0] = 16 * st["init_vertices"] + 4 * st["search_probes"]
+    # stream: 4 B per streamed entry + 8 B per counter decrement (4 B read + 4 B write)
+    dec_stream = st["stream_decrements"]
+    b[1] = 4 * st["stream_entries"] + 8 * dec_stream
+    # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;
+    # per entry 4 B; per decrement 8 B; per push 8 B queue write + 4 B row length;
+    # emission: gather 4 B old2new + 1 B mask per vertex + 4 B count per candidate;
+    # scatter 4 B count per candidate
+    dec_casc = st["decrements"] - dec_stream
+    b[2] = (28 * st["items"] + 4 * st["entries"] + 8 * dec_casc + 12 * st["pushes"]
+            + 5 * st["emit_gathered"] + 4 * st["candidates"])
+    return b
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for fn in ("peel.cu", "peel_core.cuh", "device.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2606_07148_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    dig = source_digest()
+    with open(p) as f:
+        for line in f:
+            t = line.split()
+            if len(t) >= 4 and not line.startswith("#") and t[0] == kernel and t[1] == workload:
+                return float(t[2]) if t[3] == dig else None
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------
+def make_inputs(name, device):
+    import synth
+    spec = synth.WORKLOADS[name]
+    nU, nV, eu, ev = synth.make_graph(spec, device=device)
+    return spec, nU, nV, eu, ev
+
+
+def describe(spec, name):
+    return ("Chung-Lu bipartite |U|=%d |V|=%d m=%d exponents %.1f/%.1f seed %d"
+            % (spec["nU"], spec["nV"], spec["m"], spec["gamma_u"], spec["gamma_v"], spec["seed"]))
+
+
+def peel_pairs_for(name, spec):
+    if name.startswith("billion"):
+        return [tuple(spec["pairs"][0])]
+    return [tuple(p) for p in spec["pairs"]]
+
+
+def cpu_baseline_peel(nU, nV, eu_h, ev_h, pairs, m, budget_s=25.0):
+    import oracle
+    off, adj = oracle.build_csr(nU, nV, eu_h, ev_h)
+    done = 0
+    t0 = time.perf_counter()
+    results = {}
+    for a, b in pairs:
+        results[(a, b)] = oracle.peel(nU, nV, off, adj, a, b)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done * m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d queries of one step, single-threaded oracle peel, CSR build excluded"
+                      % (done, len(pairs))}, results
+
+
+def run_peel(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2606_07148_gb300 import ABCore
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    spec, nU, nV, eu, ev = make_inputs(name, dev)
+    m = spec["m"]
+    pairs = peel_pairs_for(name, spec)
+    core = ABCore(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    core.load_edges(nU, nV, eu, ev)
+    e1.record()
+    torch.cuda.synchronize()
+    csr_ms = e0.elapsed_time(e1)
+    eu_h = eu.cpu().numpy() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    ev_h = ev.cpu().numpy() if eu_h is not None else None
+    del eu, ev
+    torch.cuda.empty_cache()
+
+    outs = [(torch.empty(nU, dtype=torch.uint8, device=dev), torch.empty(nV, dtype=torch.uint8, device=dev))
+            for _ in pairs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for (a, b), (ou, ov) in zip(pairs, outs):
+            core.compute(a, b, ou, ov, asynchronous=True)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    core.sync()
+    core.set_param("timing", 1)
+    core.set_param("reset_stats", 1)
+    st0 = core.stats()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    core.sync()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    st = core.stats()
+    core.set_param("timing", 0)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(step_ms)
+    ms = allreduce_max(ms, world, dev)
+    value = world * len(pairs) * m / (ms / 1e3) / 1e9
+
+    launches = st["launches"] - st0["launches"]
+    bytes_k = algorithmic_bytes(st)
+    kern_ms = st["kernel_ms"]
+    dom = max((k for k in (0, 1, 2)), key=lambda k: kern_ms[k])
+    n_launch = max(st["kernel_launches"][dom], 1)
+    achieved = bytes_k[dom] / n_launch / (kern_ms[dom] / n_launch / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
+    peak, peak_src = measured_peaks()
+    traffic = traffic_from_profiles(KERNEL_NAMES[dom], name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": KERNEL_NAMES[dom], "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(bytes_k[dom] / n_launch),
+                "avg_launch_ms": round(kern_ms[dom] / n_launch, 4),
+                "kernel_share": {KERNEL_NAMES[k]: round(kern_ms[k] / max(sum(kern_ms[:3]), 1e-9), 3)
+                                 for k in (0, 1, 2)}}
+
+    # end to end through the C ABI with host buffers (pinned): per step, the queries' thresholds
+    # go in as call arguments and every mask comes back to the host inside the timed region
+    host = [(torch.empty(nU, dtype=torch.uint8, pin_memory=True), torch.empty(nV, dtype=torch.uint8, pin_memory=True))
+            for _ in pairs]
+    e2e_steps = max(1, min(args.steps, 50))
+    for (a, b), (hu, hv) in zip(pairs, host):
+        core.compute(a, b, hu, hv)
+    barrier(world)
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        for (a, b), (hu, hv) in zip(pairs, host):
+            core.compute(a, b, hu, hv)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    e2e_s = allreduce_max(e2e_s, world, dev)
+    e2e = {"value": round(world * len(pairs) * m / e2e_s / 1e9, 3), "unit": "GTEPS",
+           "h2d_bytes_per_step": 8 * len(pairs), "d2h_bytes_per_step": len(pairs) * (nU + nV)}
+
+    cpu = None
+    parity = None
+    if eu_h is not None:
+        cpu, res = cpu_baseline_peel(nU, nV, eu_h, ev_h, pairs, m)
+        ok = 0
+        for (a, b), (hu, hv) in zip(pairs, host):
+            if (a, b) in res:
+                wu, wv = res[(a, b)]
+                ok += int(np.array_equal(hu.numpy(), wu) and np.array_equal(hv.numpy(), wv))
+        parity = "%d/%d queries bit-exact vs oracle" % (ok, len(res))
+
+    line = {
+        "metric": "(alpha,beta)-core peel GTEPS", "value": round(value, 3), "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": name, "graph": describe(spec, name), "queries_per_step": [list(p) for p in pairs],
+                   "csr_build_ms": round(csr_ms, 2), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before every step (256 MB write); CSR %.2f GB > 129 MB L2"
+                         % ((8 * (nU + nV + 1) + 8 * m) / 1e9),
+                   "timed_wall_s": round(t_wall, 4)},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "cpu_baseline": cpu, "parity": parity,
+        "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4)},
+    }
+    core.close()
+    return line
+
+
+def run_reference(args, rank, world, local):
+    """The CPU oracle on the same workload, metric and config (one query per step, rotating)."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    if rank != 0:
+        return None
+    name = args.workload
+    spec = synth.WORKLOADS[name]
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    nU, nV, eu, ev = synth.make_graph(spec, device=device)
+    eu, ev = eu.cpu().numpy(), ev.cpu().numpy()
+    m = spec["m"]
+    pairs = peel_pairs_for(name, spec)
+    off, adj = oracle.build_csr(nU, nV, eu, ev)
+    for i in range(args.warmup):
+        a, b = pairs[i % len(pairs)]
+        oracle.peel(nU, nV, off, adj, a, b)
+    times = []
+    t_all = time.perf_counter()
+    for i in range(args.steps):
+        a, b = pairs[i % len(pairs)]
+        t = time.perf_counter()
+        oracle.peel(nU, nV, off, adj, a, b)
+        times.append(time.perf_counter() - t)
+    s = statistics.mean(times)
+    value = m / s / 1e9
+    cpu = {"value": round(value, 4), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+           "sample": "one query per step, rotating over %s; single-threaded; CSR build excluded" % (pairs,)}
+    return {
+        "impl": "reference", "metric": "(alpha,beta)-core peel GTEPS", "value": round(value, 4), "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": name, "graph": describe(spec, name), "queries_per_step": [list(p) for p in pairs],
+                   "parallelism": "single"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "timed_wall_s": round(time.perf_counter() - t_all, 3),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="peel-4Mx2M-80M")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, world, local = dist_info()
+    import torch
+    dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world, local)
+    else:
+        from paper_2606_07148_gb300.buildlib import build
+        if rank == 0:
+            build()
+        barrier(world)
+        line = run_peel(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -52,27 +52,47 @@ extern "C" {
 
 typedef struct abcore_ctx abcore_ctx;
 
-/* Per-call device counters of the last abcore_compute / abcore_compute_batch, plus memory. */
+/* Kernel kinds, indexing abcore_stats.kernel_launches / kernel_ms. */
+#define ABCORE_K_INIT    0  /* candidate counts (row search or full degree)              */
+#define ABCORE_K_STREAM  1  /* streaming the initial violators' rows                     */
+#define ABCORE_K_CASCADE 2  /* work-queue cascade plus mask emission                     */
+#define ABCORE_K_BATCH   3  /* batched chains                                            */
+#define ABCORE_K_SERVE   4  /* on-the-fly queries and the serving loop                   */
+#define ABCORE_K_KINDS   8
+
+/* Device counters accumulated over compute calls since the context was created or since
+ * abcore_set_param(ctx, "reset_stats", 1), plus memory figures. kernel_ms is filled only while
+ * the "timing" parameter is 1: CUDA events are then recorded on the context's stream around
+ * each launch. */
 typedef struct {
-    int64_t init_vertices;   /* candidate vertices whose in-candidate degree was set           */
-    int64_t search_probes;   /* adjacency words read while counting in-candidate neighbours     */
-    int64_t stream_entries;  /* adjacency entries streamed from the initial violators' rows     */
-    int64_t entries;         /* adjacency entries read by the cascade                           */
-    int64_t decrements;      /* atomic degree decrements issued                                 */
-    int64_t pushes;          /* vertices queued for removal after the initial scan              */
-    int64_t items;           /* cascade work items (row chunks) processed                       */
-    int64_t candidates;      /* |P|: vertices that met their bound on full degree               */
-    int64_t steps;           /* batch: chain steps executed                                     */
-    int32_t mode;            /* bit 0: U counts by search, bit 1: V counts by search            */
-    int32_t grid_blocks;     /* blocks of the persistent cascade launch                         */
-    int64_t device_bytes;    /* device memory currently held by the context                     */
+    int64_t peels;           /* single peels run (a batch counts each chain step)             */
+    int64_t candidates;      /* sum of |P|: vertices meeting their bound on full degree        */
+    int64_t init_vertices;   /* candidates whose live-candidate count was set                  */
+    int64_t search_probes;   /* adjacency words read while searching candidate boundaries      */
+    int64_t stream_entries;  /* adjacency entries streamed from the initial violators' rows    */
+    int64_t entries;         /* adjacency entries read by the cascade                          */
+    int64_t decrements;      /* atomic count decrements, all kernels                           */
+    int64_t stream_decrements; /* of which issued while streaming the initial violators' rows  */
+    int64_t pushes;          /* vertices queued for removal                                    */
+    int64_t items;           /* cascade work items (row chunks) processed                      */
+    int64_t emit_gathered;   /* mask bytes written by a gather over every vertex               */
+    int64_t emit_scattered;  /* candidates checked by a scatter of survivors into zeroed masks */
+    int64_t mask_zeroed;     /* mask bytes cleared before a scatter                            */
+    int64_t launches;        /* kernels launched                                               */
+    int64_t kernel_launches[ABCORE_K_KINDS];  /* timed launches per kernel kind                */
+    double kernel_ms[ABCORE_K_KINDS];         /* device milliseconds per kernel kind           */
+    int32_t mode;            /* last peel: bit 0 U counts by search, bit 1 V counts by search  */
+    int32_t grid_blocks;     /* blocks of the persistent cascade launch                        */
+    int64_t device_bytes;    /* device memory held by the context now                          */
     int64_t peak_device_bytes;
 } abcore_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to order all work
- * on, or NULL for a stream the context creates and owns. *out receives the context. */
+ * on (cudaStreamLegacy and cudaStreamPerThread are accepted), or NULL for a stream the context
+ * creates and owns. Device buffers passed to later calls must be ready in that stream's order.
+ * *out receives the context. */
 int abcore_create(abcore_ctx **out, int device, void *cuda_stream);
 
 /* Release every device and host resource of the context. NULL is accepted. */
@@ -166,7 +186,7 @@ int abcore_serve_stop(abcore_ctx *ctx);
 
 /* ---- introspection ----------------------------------------------------------------------- */
 
-/* Counters of the last compute call and the context's device memory. */
+/* Accumulated counters (see abcore_stats) and the context's device memory. */
 int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
 
 /* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown. */

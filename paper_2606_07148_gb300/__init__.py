@@ -30,9 +30,17 @@ class ABCore:
     """One library context on one CUDA device, ordered on one stream."""
 
     def __init__(self, device: int = 0, stream=None):
+        """Work is ordered on ``stream`` (default: torch's current stream on ``device``), so
+        tensors produced by torch on that stream are complete before the library reads them."""
         abi.load_library()
+        torch = _torch()
         self._h = ctypes.c_void_p()
-        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        # torch reports its legacy default stream as handle 0; the C ABI reads NULL as "create a
+        # private stream", so pass cudaStreamLegacy (handle 1) for it instead.
+        self.stream = stream
+        s = ctypes.c_void_p(stream.cuda_stream or 1)
         rc = abi.abcore_create(ctypes.byref(self._h), device, s)
         if rc != 0:
             raise ABCoreError(rc, "abcore_create failed")

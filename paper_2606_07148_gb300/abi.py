@@ -35,18 +35,28 @@ EXPORTED = [
 ]
 
 
+K_INIT, K_STREAM, K_CASCADE, K_BATCH, K_SERVE = 0, 1, 2, 3, 4
+K_KINDS = 8
+
+
 class abcore_stats(ctypes.Structure):
     _fields_ = [
-        ("init_vertices", ctypes.c_int64), ("search_probes", ctypes.c_int64),
-        ("stream_entries", ctypes.c_int64), ("entries", ctypes.c_int64),
-        ("decrements", ctypes.c_int64), ("pushes", ctypes.c_int64), ("items", ctypes.c_int64),
-        ("candidates", ctypes.c_int64), ("steps", ctypes.c_int64), ("mode", ctypes.c_int32),
-        ("grid_blocks", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-        ("peak_device_bytes", ctypes.c_int64),
+        ("peels", ctypes.c_int64), ("candidates", ctypes.c_int64), ("init_vertices", ctypes.c_int64),
+        ("search_probes", ctypes.c_int64), ("stream_entries", ctypes.c_int64), ("entries", ctypes.c_int64),
+        ("decrements", ctypes.c_int64), ("stream_decrements", ctypes.c_int64), ("pushes", ctypes.c_int64),
+        ("items", ctypes.c_int64),
+        ("emit_gathered", ctypes.c_int64), ("emit_scattered", ctypes.c_int64), ("mask_zeroed", ctypes.c_int64),
+        ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64 * K_KINDS),
+        ("kernel_ms", ctypes.c_double * K_KINDS), ("mode", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+        ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 class abcore_req(ctypes.Structure):

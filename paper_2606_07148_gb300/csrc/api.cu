@@ -171,6 +171,7 @@ int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *mask_u
     if ((g.nU > 0 && !mask_u) || (g.nV > 0 && !mask_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
     const bool dev = ptr_on_device(flags);
     if ((flags & ABCORE_ASYNC) && !dev) return ctx->fail(ABCORE_EINVAL, "ABCORE_ASYNC needs device pointers");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
     if (g.n() == 0) return ABCORE_OK;
     if (dev) return peel_compute(ctx, alpha, beta, mask_u, mask_v, !(flags & ABCORE_ASYNC));
     ABC_TRY(peel_finish(ctx));
@@ -197,6 +198,7 @@ int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, cons
     if ((g.nU > 0 && !masks_u) || (g.nV > 0 && !masks_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
     const bool dev = ptr_on_device(flags);
     if ((flags & ABCORE_ASYNC) && !dev) return ctx->fail(ABCORE_EINVAL, "ABCORE_ASYNC needs device pointers");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
     if (g.n() == 0) return ABCORE_OK;
     ABC_TRY(peel_finish(ctx));
     if (dev) return batch_compute(ctx, n, alphas, betas, masks_u, masks_v, !(flags & ABCORE_ASYNC));
@@ -315,6 +317,16 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         if (value < 0) return ctx->fail(ABCORE_EINVAL, "batch_groups must be >= 0");
         p.batch_groups = (int)value;
         free_batch(ctx);
+    } else if (k == "timing") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "timing must be 0 or 1");
+        ABC_TRY(abcore_sync(ctx));
+        p.timing = (int)value;
+    } else if (k == "reset_stats") {
+        ABC_TRY(abcore_sync(ctx));
+        const int32_t mode = ctx->stats.mode, grid = ctx->stats.grid_blocks;
+        ctx->stats = abcore_stats{};
+        ctx->stats.mode = mode;
+        ctx->stats.grid_blocks = grid;
     } else if (k == "debug_stall_slots") {
         if (value < 0 || value > 32) return ctx->fail(ABCORE_EINVAL, "debug_stall_slots must be 0..32");
         p.debug_stall_slots = (int)value;
@@ -342,6 +354,7 @@ int abcore_export_csr(abcore_ctx *ctx, int64_t *off, int32_t *adj, int32_t *new2
     ABC_CU(cudaSetDevice(ctx->device));
     ABC_TRY(require_graph(ctx));
     ABC_TRY(abcore_sync(ctx));
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
     const Graph &g = ctx->g;
     const cudaMemcpyKind kind = ptr_on_device(flags) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (off) ABC_CU(cudaMemcpyAsync(off, g.off, sizeof(int64_t) * (g.n() + 1), kind, ctx->stream));

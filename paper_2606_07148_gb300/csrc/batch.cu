@@ -1,16 +1,613 @@
-// Batched (alpha, beta)-cores. Placeholder: one peel per pair, in order.
+// Batched (alpha, beta)-cores: many pairs over one graph in one persistent launch, replayed as a
+// CUDA graph.
+//
+// Nested property (Section 4.2, the basis of Lemma 1): if alpha' >= alpha and beta' >= beta then
+// core(alpha', beta') lies inside core(alpha, beta); and for any vertex set S containing
+// core(alpha, beta), peeling G[S] gives the same core as peeling G. Algorithm 2 (GCC+) uses this
+// with core numbers; here it is applied along chains: pairs that share alpha are sorted by beta,
+// and one chain peels (alpha, beta_0) and then raises the V bound step by step, each step
+// starting from the previous step's core. A vertex is removed at most once per chain, so a
+// chain costs at most one full peel, whatever its length. The step at which each vertex falls
+// is recorded (lvl), and the masks of all the chain's pairs follow from it:
+//     x in core(alpha, beta_j)  <=>  x is a step-0 candidate and lvl[x] > j.
+//
+// The chains run concurrently, each on its own group of blocks of one cooperative launch. Inside
+// a group, steps are separated by a bounded group barrier; the cascade of each step reuses the
+// single peel's work queue (peel_core.cuh). A second kernel writes every pair's masks in the
+// caller's ids. Memsets, both launches and the status read-back are captured once per pair list
+// as a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "device.cuh"
 #include "internal.h"
+#include "peel_core.cuh"
 
-struct BatchState {};
+namespace {
 
-int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
-                  uint8_t *d_masks_u, uint8_t *d_masks_v, bool sync_and_check) {
-    (void)sync_and_check;
+using abc::LaneStats;
+using abc::WarpSmem;
+
+constexpr int BATCH_THREADS = 256;
+constexpr int MAX_CHAINS_PER_WAVE = 32;
+constexpr int MAX_STEPS = 255;
+
+struct ChainDev {
+    int32_t alpha;
+    int32_t nsteps;
+    int32_t beta_off;        // betas[beta_off .. beta_off + nsteps): ascending V bounds
+    int32_t pU0, pV0;        // step-0 candidate prefixes
+    int32_t searchU, searchV;
+    int32_t first_block, nblocks;
+    int32_t col;             // column of this chain in lvl
+    int64_t sa, ea, sb, eb;  // step-0 violator slices (see stream_range)
+};
+
+struct ChainMem {
+    int2 *cp;
+    unsigned long long *q;
+    PeelCtl *ctl;
+    unsigned *bar;           // group barrier: [0] arrivals, [32] generation
+};
+
+struct BatchArgs {
+    const int64_t *off;
+    const int32_t *adj;
+    int32_t nU, nV;
+    const ChainDev *chains;
+    const ChainMem *mem;
+    const int32_t *betas;
+    int32_t nchains;
+    uint8_t *lvl;
+    int32_t lvl_stride;
+    int32_t chunk;
+    long long qcap;
+    unsigned long long timeout_ns;
+};
+
+// Bounded barrier over the `G` blocks of one chain. The last block to arrive can run `fixup`
+// while every other block of the group waits. Returns false if the group saw an error.
+__device__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl, bool fixup, unsigned long long timeout_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *genp = bar + 32;
+        const unsigned gen = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == (unsigned)G - 1) {
+            atomicExch(bar, 0u);
+            if (fixup) {
+                // tickets handed out but never filled lie in [tail, head): skip them so the next
+                // step's pushes land in slots nobody holds
+                const unsigned long long h = abc::ld_relaxed(&ctl->head);
+                const unsigned long long t = abc::ld_relaxed(&ctl->tail);
+                const unsigned long long mx = h > t ? h : t;
+                atomicExch(&ctl->head, mx);
+                atomicExch(&ctl->tail, mx);
+                atomicExch(&ctl->done, mx);
+            }
+            __threadfence();
+            atomicAdd(bar + 32, 1u);
+        } else {
+            const unsigned long long t0 = abc::now_ns();
+            unsigned sl = 32;
+            while (*genp == gen) {
+                if (abc::now_ns() - t0 > timeout_ns) {
+                    abc::set_error(&ctl->err, ABCORE_ETIMEDOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(sl);
+                if (sl < 512) sl <<= 1;
+            }
+        }
+        __threadfence();
+        if (abc::ld_relaxed_i32(&ctl->err) != 0) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
+    __shared__ WarpSmem smem[BATCH_THREADS / 32];
+    int c = 0;
+    while (c + 1 < B.nchains && (int)blockIdx.x >= B.chains[c + 1].first_block) ++c;
+    const ChainDev cd = B.chains[c];
+    const ChainMem mem = B.mem[c];
+    const int G = cd.nblocks;
+    const int r = (int)blockIdx.x - cd.first_block;
+    const int wib = threadIdx.x >> 5;
+
+    PeelArgs a{};
+    a.off = B.off;
+    a.adj = B.adj;
+    a.cp = mem.cp;
+    a.q = mem.q;
+    a.qcap = B.qcap;
+    a.ctl = mem.ctl;
+    a.nU = B.nU;
+    a.nV = B.nV;
+    a.pU = cd.pU0;
+    a.pV = cd.pV0;
+    a.thrU = cd.alpha;
+    a.thrV = B.betas[cd.beta_off];
+    a.chunk = B.chunk;
+    a.searchU = cd.searchU;
+    a.searchV = cd.searchV;
+    a.timeout_ns = B.timeout_ns;
+    a.skip_zero = 0;  // a V bound of 0 may rise later: keep every count exact
+    a.lvl = B.lvl;
+    a.lvl_stride = B.lvl_stride;
+    a.lvl_col = cd.col;
+    a.step = 0;
+    const int grab_div = max(1, G * (BATCH_THREADS / 32) / 8);
+
+    const int64_t t0 = (int64_t)r * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)G * blockDim.x;
+    LaneStats ls;
+    unsigned long long probes = 0, inits = 0, ents = 0, sdecs = 0;
+
+    abc::init_range(a, t0, nthreads, ls, probes, inits);
+    if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+    if (cd.ea > cd.sa || cd.eb > cd.sb) {
+        const unsigned long long d0 = ls.decs;
+        abc::stream_range(a, cd.sa, cd.ea, cd.sb, cd.eb, t0, nthreads, ls, ents);
+        sdecs = ls.decs - d0;
+        ls.decs = d0;
+        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+    }
+    // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
+    // block waits on warps that left, and the barrier reports the error to all of them.
+    (void)abc::cascade_loop(a, smem[wib], ls, grab_div);
+    if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+    for (int j = 1; j < cd.nsteps; ++j) {
+        const int32_t prev = a.thrV;
+        a.thrV = B.betas[cd.beta_off + j];
+        a.step = j;
+        // V vertices alive after step j-1 (count >= previous bound) that miss the new bound
+        for (int64_t b = t0 - (threadIdx.x & 31); b < cd.pV0; b += nthreads) {
+            const int64_t i = b + (threadIdx.x & 31);
+            bool viol = false;
+            int32_t x = 0;
+            int nch = 0;
+            if (i < cd.pV0) {
+                x = (int32_t)(B.nU + i);
+                const int2 v = __ldcg(&a.cp[x]);
+                viol = v.x >= prev && v.x < a.thrV;
+                nch = abc::chunks_of(v.y, a.chunk);
+            }
+            abc::warp_push(a, viol, x, nch, ls);
+        }
+        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        (void)abc::cascade_loop(a, smem[wib], ls, grab_div);
+        if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+    }
+out:
+    abc::flush_stats(a, ls);
+    {
+        unsigned long long v[4] = {inits, probes, ents, sdecs};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (unsigned long long)abc::warp_sum64((long long)v[i]);
+        if ((threadIdx.x & 31) == 0) {
+            if (v[0]) atomicAdd(&a.ctl->st[ST_INIT], v[0]);
+            if (v[1]) atomicAdd(&a.ctl->st[ST_PROBES], v[1]);
+            if (v[2]) atomicAdd(&a.ctl->st[ST_STREAM], v[2]);
+            if (v[3]) atomicAdd(&a.ctl->st[ST_SDECS], v[3]);
+        }
+        if (r == 0 && threadIdx.x == 0) atomicAdd(&a.ctl->st[ST_STEPS], (unsigned long long)cd.nsteps);
+    }
+}
+
+struct PairRef {
+    int32_t chain;  // index into the wave's chains
+    int32_t step;
+};
+
+// Masks of every pair of a wave, in the caller's ids: one thread per vertex, one byte per pair.
+__global__ void __launch_bounds__(256) k_batch_emit(const int32_t *__restrict__ old2new, int32_t nU, int32_t nV,
+                                                    const uint8_t *__restrict__ lvl, int32_t lvl_stride,
+                                                    const ChainDev *__restrict__ chains, int32_t nchains,
+                                                    const PairRef *__restrict__ pairs, const int32_t *__restrict__ pidx,
+                                                    int32_t npairs, uint8_t *__restrict__ masks_u,
+                                                    uint8_t *__restrict__ masks_v) {
+    extern __shared__ int32_t sh[];
+    int32_t *pU0 = sh, *pV0 = sh + nchains, *col = sh + 2 * nchains;
+    int32_t *pc = sh + 3 * nchains, *ps = pc + npairs, *pi = ps + npairs;
+    for (int i = threadIdx.x; i < nchains; i += blockDim.x) {
+        pU0[i] = chains[i].pU0;
+        pV0[i] = chains[i].pV0;
+        col[i] = chains[i].col;
+    }
+    for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+        pc[i] = pairs[i].chain;
+        ps[i] = pairs[i].step;
+        pi[i] = pidx[i];
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)nU + nV;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = __ldg(&old2new[i]);
+        const bool upper = i < nU;
+        const uint8_t *row = lvl + (size_t)x * lvl_stride;
+        for (int p = 0; p < npairs; ++p) {
+            const int ch = pc[p];
+            const bool cand = upper ? (x < pU0[ch]) : (x - nU < pV0[ch]);
+            const uint8_t v = (cand && __ldg(&row[col[ch]]) > ps[p]) ? 1 : 0;
+            if (upper) masks_u[(size_t)pi[p] * nU + i] = v;
+            else masks_v[(size_t)pi[p] * nV + (i - nU)] = v;
+        }
+    }
+}
+
+}  // namespace
+
+// One wave: up to MAX_CHAINS_PER_WAVE chains sharing the device at once.
+struct Wave {
+    std::vector<ChainDev> chains;
+    std::vector<PairRef> pairs;
+    std::vector<int32_t> pidx;   // caller pair index of each PairRef
+    ChainDev *d_chains = nullptr;
+    PairRef *d_pairs = nullptr;
+    int32_t *d_pidx = nullptr;
+    int grid = 0;
+};
+
+struct BatchState {
+    // key of the captured graph
+    std::vector<int32_t> key_a, key_b;
+    uint8_t *key_mu = nullptr, *key_mv = nullptr;
+    int64_t key_graph_n = -1, key_graph_m = -1;
+    int key_chunk = 0;
+    // plan
+    std::vector<Wave> waves;
+    std::vector<int32_t> betas;
+    int32_t *d_betas = nullptr;
+    int nmem = 0;                       // chain workspaces allocated
+    std::vector<ChainMem> mem;
+    ChainMem *d_mem = nullptr;
+    uint8_t *lvl = nullptr;
+    int lvl_stride = 0;
+    PeelCtl *ctl_host = nullptr;        // pinned: [waves x MAX_CHAINS_PER_WAVE]
+    long long qcap = 0;
+    bool q_dirty = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static void destroy_plan(abcore_ctx *ctx, BatchState *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    for (auto &w : b->waves) {
+        ctx->release(w.d_chains);
+        ctx->release(w.d_pairs);
+        ctx->release(w.d_pidx);
+    }
+    b->waves.clear();
+    ctx->release(b->d_betas);
+    if (b->ctl_host) cudaFreeHost(b->ctl_host);
+    b->ctl_host = nullptr;
+    b->key_a.clear();
+    b->key_b.clear();
+    b->key_graph_n = -1;
+}
+
+void free_batch(abcore_ctx *ctx) {
+    BatchState *b = ctx->batch;
+    if (!b) return;
+    cudaStreamSynchronize(ctx->stream);
+    destroy_plan(ctx, b);
+    for (auto &m : b->mem) {
+        ctx->release(m.cp);
+        ctx->release(m.q);
+        ctx->release(m.ctl);
+        ctx->release(m.bar);
+    }
+    ctx->release(b->d_mem);
+    ctx->release(b->lvl);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+    ctx->batch = nullptr;
+}
+
+static int batch_grid(abcore_ctx *ctx) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, 0);
+    if (ctx->prm.blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->prm.blocks_per_sm);
+    return std::max(per_sm, 1) * ctx->num_sms;
+}
+
+// Build the plan for a pair list: chains by alpha, waves, slices, device tables.
+static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *alphas, const int32_t *betas) {
     const Graph &g = ctx->g;
-    for (int32_t i = 0; i < n; ++i)
-        ABC_TRY(peel_compute(ctx, alphas[i], betas[i], d_masks_u + (size_t)i * g.nU,
-                             d_masks_v + (size_t)i * g.nV, true));
+    std::map<int32_t, std::vector<int32_t>> by_alpha;
+    for (int32_t i = 0; i < n; ++i) by_alpha[alphas[i]].push_back(betas[i]);
+    struct Chain {
+        int32_t alpha;
+        std::vector<int32_t> betas;
+    };
+    std::vector<Chain> chains;
+    for (auto &kv : by_alpha) {
+        std::vector<int32_t> bs = kv.second;
+        std::sort(bs.begin(), bs.end());
+        bs.erase(std::unique(bs.begin(), bs.end()), bs.end());
+        for (size_t s = 0; s < bs.size(); s += MAX_STEPS)
+            chains.push_back({kv.first, std::vector<int32_t>(bs.begin() + s, bs.begin() + std::min(bs.size(), s + MAX_STEPS))});
+    }
+    const int C = (int)chains.size();
+    const int grid = batch_grid(ctx);
+    const int per_wave = std::max(1, std::min({MAX_CHAINS_PER_WAVE, grid, b->nmem}));
+    b->betas.clear();
+    b->waves.clear();
+    for (int w0 = 0; w0 < C; w0 += per_wave) {
+        Wave wave;
+        const int cw = std::min(per_wave, C - w0);
+        wave.grid = grid;
+        int first = 0;
+        for (int k = 0; k < cw; ++k) {
+            const Chain &ch = chains[w0 + k];
+            ChainDev d{};
+            d.alpha = ch.alpha;
+            d.nsteps = (int32_t)ch.betas.size();
+            d.beta_off = (int32_t)b->betas.size();
+            b->betas.insert(b->betas.end(), ch.betas.begin(), ch.betas.end());
+            const int32_t beta0 = ch.betas[0];
+            d.pU0 = (int32_t)cnt_ge(g.cntU_ge, ch.alpha);
+            d.pV0 = (int32_t)cnt_ge(g.cntV_ge, beta0);
+            const int mode = pick_mode(ctx, ch.alpha, beta0, d.pU0, d.pV0);
+            d.searchU = mode & 1;
+            d.searchV = (mode >> 1) & 1;
+            if (!d.searchU && d.pU0 > 0) {
+                d.sa = g.m + cnt_ge(g.edgesV_ge, beta0);
+                d.ea = 2 * g.m;
+            }
+            if (!d.searchV && d.pV0 > 0) {
+                d.sb = cnt_ge(g.edgesU_ge, ch.alpha);
+                d.eb = g.m;
+            }
+            d.nblocks = grid / cw + (k < grid % cw ? 1 : 0);
+            d.first_block = first;
+            first += d.nblocks;
+            d.col = k;
+            wave.chains.push_back(d);
+        }
+        b->waves.push_back(std::move(wave));
+    }
+    // pair -> (wave, chain in wave, step)
+    for (int32_t i = 0; i < n; ++i) {
+        int ci = 0;
+        for (; ci < C; ++ci) {
+            if (chains[ci].alpha != alphas[i]) continue;
+            const auto &bs = chains[ci].betas;
+            if (std::binary_search(bs.begin(), bs.end(), betas[i])) break;
+        }
+        const int wv = ci / per_wave, k = ci % per_wave;
+        const auto &bs = chains[ci].betas;
+        const int step = (int)(std::lower_bound(bs.begin(), bs.end(), betas[i]) - bs.begin());
+        b->waves[wv].pairs.push_back({k, step});
+        b->waves[wv].pidx.push_back(i);
+    }
+    ABC_TRY(ctx->alloc(&b->d_betas, b->betas.size(), "batch betas"));
+    ABC_CU(cudaMemcpy(b->d_betas, b->betas.data(), sizeof(int32_t) * b->betas.size(), cudaMemcpyHostToDevice));
+    for (auto &w : b->waves) {
+        ABC_TRY(ctx->alloc(&w.d_chains, w.chains.size(), "batch chains"));
+        ABC_TRY(ctx->alloc(&w.d_pairs, std::max<size_t>(w.pairs.size(), 1), "batch pairs"));
+        ABC_TRY(ctx->alloc(&w.d_pidx, std::max<size_t>(w.pidx.size(), 1), "batch pairs"));
+        ABC_CU(cudaMemcpy(w.d_chains, w.chains.data(), sizeof(ChainDev) * w.chains.size(), cudaMemcpyHostToDevice));
+        if (!w.pairs.empty()) {
+            ABC_CU(cudaMemcpy(w.d_pairs, w.pairs.data(), sizeof(PairRef) * w.pairs.size(), cudaMemcpyHostToDevice));
+            ABC_CU(cudaMemcpy(w.d_pidx, w.pidx.data(), sizeof(int32_t) * w.pidx.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    ABC_CU(cudaMallocHost(&b->ctl_host, sizeof(PeelCtl) * MAX_CHAINS_PER_WAVE * b->waves.size()));
     return ABCORE_OK;
 }
 
-void free_batch(abcore_ctx *ctx) { (void)ctx; }
+// Chain workspaces: counts, queue, control block and barrier per concurrent chain, plus lvl.
+static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    const int grid = batch_grid(ctx);
+    const long long qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 +
+                           (long long)MAX_STEPS * 2 * grid * (BATCH_THREADS / 32) * 32 / std::max(want_chains, 1) + 4096;
+    if (b->nmem >= want_chains && b->qcap >= qcap) return ABCORE_OK;
+    for (auto &m : b->mem) {
+        ctx->release(m.cp);
+        ctx->release(m.q);
+        ctx->release(m.ctl);
+        ctx->release(m.bar);
+    }
+    b->mem.clear();
+    ctx->release(b->d_mem);
+    ctx->release(b->lvl);
+    b->nmem = 0;
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    const double per_chain = 8.0 * n + 8.0 * qcap + 1.0 * n;
+    int fit = (int)std::max(1.0, 0.6 * (double)freeb / per_chain);
+    const int chains = std::max(1, std::min(want_chains, fit));
+    b->qcap = qcap;
+    b->mem.resize(chains);
+    for (int c = 0; c < chains; ++c) {
+        ChainMem &m = b->mem[c];
+        ABC_TRY(ctx->alloc(&m.cp, (size_t)std::max<int64_t>(n, 1), "batch counts"));
+        ABC_TRY(ctx->alloc(&m.q, (size_t)qcap, "batch queue"));
+        ABC_TRY(ctx->alloc(&m.ctl, 1, "batch control"));
+        ABC_TRY(ctx->alloc(&m.bar, 64, "batch barrier"));
+        ABC_CU(cudaMemsetAsync(m.q, 0xff, sizeof(unsigned long long) * (size_t)qcap, ctx->stream));
+        ABC_CU(cudaMemsetAsync(m.bar, 0, 64 * sizeof(unsigned), ctx->stream));
+    }
+    ABC_TRY(ctx->alloc(&b->d_mem, chains, "batch chain table"));
+    ABC_CU(cudaMemcpy(b->d_mem, b->mem.data(), sizeof(ChainMem) * chains, cudaMemcpyHostToDevice));
+    b->lvl_stride = ((std::min(chains, MAX_CHAINS_PER_WAVE) + 3) / 4) * 4;
+    ABC_TRY(ctx->alloc(&b->lvl, (size_t)std::max<int64_t>(n, 1) * b->lvl_stride, "batch levels"));
+    b->nmem = chains;
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    return ABCORE_OK;
+}
+
+// Enqueue the whole batch on the stream (captured into a graph on first use).
+static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t *d_mv) {
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+        Wave &w = b->waves[wi];
+        const int cw = (int)w.chains.size();
+        for (int c = 0; c < cw; ++c) {
+            ABC_CU(cudaMemsetAsync(b->mem[c].ctl, 0, sizeof(PeelCtl), ctx->stream));
+            ABC_CU(cudaMemsetAsync(b->mem[c].bar, 0, 64 * sizeof(unsigned), ctx->stream));
+        }
+        ABC_CU(cudaMemsetAsync(b->lvl, 0xff, (size_t)n * b->lvl_stride, ctx->stream));
+        BatchArgs B{};
+        B.off = g.off;
+        B.adj = g.adj;
+        B.nU = g.nU;
+        B.nV = g.nV;
+        B.chains = w.d_chains;
+        B.mem = b->d_mem;
+        B.betas = b->d_betas;
+        B.nchains = cw;
+        B.lvl = b->lvl;
+        B.lvl_stride = b->lvl_stride;
+        B.chunk = std::max(ctx->prm.chunk, 32);
+        B.qcap = b->qcap;
+        B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
+        void *args[] = {&B};
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(w.grid);
+        cfg.blockDim = dim3(BATCH_THREADS);
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ABC_CU(cudaLaunchKernelExC(&cfg, (const void *)k_batch, args));
+        ctx->stats.launches++;
+        if (!w.pairs.empty()) {
+            const int np = (int)w.pairs.size();
+            const size_t shm = sizeof(int32_t) * (3 * cw + 3 * np);
+            if (shm > 200 * 1024) return ctx->fail(ABCORE_EINVAL, "too many pairs in one batch wave");
+            if (shm > 48 * 1024)
+                ABC_CU(cudaFuncSetAttribute(k_batch_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            const int eg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
+            k_batch_emit<<<std::max(eg, 1), 256, shm, ctx->stream>>>(g.old2new, g.nU, g.nV, b->lvl, b->lvl_stride,
+                                                                     w.d_chains, cw, w.d_pairs, w.d_pidx, np, d_mu, d_mv);
+            ctx->stats.launches++;
+        }
+        for (int c = 0; c < cw; ++c)
+            ABC_CU(cudaMemcpyAsync(b->ctl_host + wi * MAX_CHAINS_PER_WAVE + c, b->mem[c].ctl, sizeof(PeelCtl),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return ABCORE_OK;
+}
+
+int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint8_t *d_masks_u,
+                  uint8_t *d_masks_v, bool sync_and_check) {
+    const Graph &g = ctx->g;
+    if (!ctx->batch) ctx->batch = new BatchState();
+    BatchState *b = ctx->batch;
+    const bool same = b->exec && b->key_mu == d_masks_u && b->key_mv == d_masks_v && b->key_graph_n == g.n() &&
+                      b->key_graph_m == g.m && b->key_chunk == ctx->prm.chunk &&
+                      b->key_a == std::vector<int32_t>(alphas, alphas + n) &&
+                      b->key_b == std::vector<int32_t>(betas, betas + n);
+    if (!same || !b->use_graph) {
+        destroy_plan(ctx, b);
+        std::map<int32_t, int> na;
+        for (int32_t i = 0; i < n; ++i) na[alphas[i]]++;
+        ABC_TRY(ensure_memory(ctx, b, std::min<int>((int)na.size(), MAX_CHAINS_PER_WAVE)));
+        ABC_TRY(make_plan(ctx, b, n, alphas, betas));
+        b->key_a.assign(alphas, alphas + n);
+        b->key_b.assign(betas, betas + n);
+        b->key_mu = d_masks_u;
+        b->key_mv = d_masks_v;
+        b->key_graph_n = g.n();
+        b->key_graph_m = g.m;
+        b->key_chunk = ctx->prm.chunk;
+        if (b->use_graph) {
+            cudaStreamCaptureStatus cs;
+            ABC_CU(cudaStreamIsCapturing(ctx->stream, &cs));
+            if (cs == cudaStreamCaptureStatusNone &&
+                cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int64_t l0 = ctx->stats.launches;
+                int rc = enqueue_batch(ctx, b, d_masks_u, d_masks_v);
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+                ctx->stats.launches = l0;
+                if (rc == ABCORE_OK && e == cudaSuccess &&
+                    cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) {
+                    b->graph = graph;
+                } else {
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    b->exec = nullptr;
+                    b->use_graph = false;  // capture refused: launch directly from now on
+                }
+            } else {
+                cudaGetLastError();
+                b->use_graph = false;
+            }
+        }
+    }
+    if (b->q_dirty) {
+        for (auto &m : b->mem) ABC_CU(cudaMemsetAsync(m.q, 0xff, sizeof(unsigned long long) * (size_t)b->qcap, ctx->stream));
+        b->q_dirty = false;
+    }
+    const bool timed = ctx->prm.timing != 0;
+    if (timed) {
+        if (!b->ev0) ABC_CU(cudaEventCreate(&b->ev0));
+        if (!b->ev1) ABC_CU(cudaEventCreate(&b->ev1));
+        ABC_CU(cudaEventRecord(b->ev0, ctx->stream));
+    }
+    if (b->exec) {
+        ABC_CU(cudaGraphLaunch(b->exec, ctx->stream));
+        for (auto &w : b->waves) ctx->stats.launches += 1 + (w.pairs.empty() ? 0 : 1);
+    } else {
+        ABC_TRY(enqueue_batch(ctx, b, d_masks_u, d_masks_v));
+    }
+    if (timed) ABC_CU(cudaEventRecord(b->ev1, ctx->stream));
+    ABC_CU(cudaGetLastError());
+    (void)sync_and_check;
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    int first_err = 0;
+    abcore_stats &s = ctx->stats;
+    for (size_t wi = 0; wi < b->waves.size(); ++wi)
+        for (size_t c = 0; c < b->waves[wi].chains.size(); ++c) {
+            const PeelCtl &pc = b->ctl_host[wi * MAX_CHAINS_PER_WAVE + c];
+            if (pc.err && !first_err) first_err = pc.err;
+            s.peels += (int64_t)pc.st[ST_STEPS];
+            s.candidates += b->waves[wi].chains[c].pU0 + b->waves[wi].chains[c].pV0;
+            s.init_vertices += (int64_t)pc.st[ST_INIT];
+            s.search_probes += (int64_t)pc.st[ST_PROBES];
+            s.stream_entries += (int64_t)pc.st[ST_STREAM];
+            s.entries += (int64_t)pc.st[ST_ENTRIES];
+            s.decrements += (int64_t)pc.st[ST_DECS] + (int64_t)pc.st[ST_SDECS];
+            s.stream_decrements += (int64_t)pc.st[ST_SDECS];
+            s.pushes += (int64_t)pc.st[ST_PUSHES];
+            s.items += (int64_t)pc.st[ST_ITEMS];
+        }
+    for (auto &w : b->waves) s.emit_gathered += (int64_t)w.pairs.size() * g.n();
+    if (timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) {
+            s.kernel_ms[ABCORE_K_BATCH] += ms;
+            s.kernel_launches[ABCORE_K_BATCH]++;
+        }
+    }
+    if (first_err) {
+        b->q_dirty = true;
+        if (first_err == ABCORE_ETIMEDOUT)
+            return ctx->fail(ABCORE_ETIMEDOUT, "batch: a bounded device wait expired (limit %lld ms)",
+                             (long long)ctx->prm.timeout_ms);
+        return ctx->fail(first_err, "batch: device reported error %d", first_err);
+    }
+    return ABCORE_OK;
+}

@@ -13,13 +13,18 @@
 #include "../../include/abcore.h"
 
 // Device-side control block of one peel (queue counters, error word, counters for stats).
+// Each hot word sits on its own 128-byte line: pushers add to tail, workers add to done, idle
+// warps poll both, and tickets come from head.
 struct PeelCtl {
-    unsigned long long head;   // next queue slot to hand out
+    unsigned long long head;   // next queue ticket to hand out
+    unsigned long long pad0[15];
     unsigned long long tail;   // queue slots reserved by pushers
+    unsigned long long pad1[15];
     unsigned long long done;   // queue slots fully processed
+    unsigned long long pad2[15];
     int err;                   // first error code (0 = none)
-    int pad;
-    unsigned long long st[8];  // stat counters, see ST_* below
+    int pad3[31];
+    unsigned long long st[12]; // stat counters, see ST_* below
 };
 enum {
     ST_INIT = 0,     // candidate vertices initialised
@@ -30,6 +35,7 @@ enum {
     ST_PUSHES = 5,   // vertices queued
     ST_ITEMS = 6,    // cascade work items processed
     ST_STEPS = 7,    // chain steps (batch)
+    ST_SDECS = 8,    // atomic decrements issued by the violator stream
 };
 
 // Everything a peel kernel needs, passed by value.
@@ -53,7 +59,12 @@ struct PeelArgs {
     const int32_t *new2old;  // [n] internal id -> caller per-layer id
     uint8_t *mask_u, *mask_v;
     int32_t emit;            // 0 none, 1 gather over all vertices, 2 scatter of live candidates
-    int32_t pad;
+    int32_t skip_zero;       // 1: no decrements toward a layer whose threshold is 0
+    // batched chains: a vertex queued during chain step `step` records it in
+    // lvl[vertex * lvl_stride + lvl_col] (lvl == nullptr: no record)
+    uint8_t *lvl;
+    int32_t lvl_stride, lvl_col, step;
+    int32_t pad2;
 };
 
 struct Params {
@@ -67,6 +78,7 @@ struct Params {
     double probe_bytes = 64.0;     // cost model: bytes per search probe
     int batch_groups = 0;      // 0 = one group per chain
     int debug_stall_slots = 0; // test hook: queue slots reserved but never written
+    int timing = 0;            // 1: CUDA events around each launch, summed into stats.kernel_ms
 };
 
 struct Graph {
@@ -86,6 +98,13 @@ struct Graph {
 
 constexpr int CTL_RING = 64;  // peels that may be in flight (ABCORE_ASYNC) before a forced wait
 
+// Host-side record of one peel in flight, turned into stats when it finishes.
+struct SlotInfo {
+    int64_t cands = 0, n = 0;
+    int emit = 0;
+    bool timed = false, has_init = false, has_stream = false;
+};
+
 struct PeelWork {
     int64_t n = 0, qcap = 0;
     int2 *cp = nullptr;
@@ -93,6 +112,9 @@ struct PeelWork {
     PeelCtl *ctl = nullptr;        // [CTL_RING] device control blocks
     PeelCtl *ctl_host = nullptr;   // [CTL_RING] pinned readback
     bool pending[CTL_RING] = {};
+    SlotInfo info[CTL_RING];
+    cudaEvent_t ev[CTL_RING][4] = {};  // created on first timed use: before init, after init,
+                                       // before cascade, after cascade
     int next = 0, last = -1;
     uint8_t *stage = nullptr;      // [n] staging for host-pointer masks
     bool q_dirty = false;          // queue not known to be all-empty
@@ -205,6 +227,7 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
 int serve_submit(abcore_ctx *ctx, const abcore_req *reqs, int32_t n, uint64_t *seq_out);
 int serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out);
 int serve_stop(abcore_ctx *ctx);
+int serve_materialize(abcore_ctx *ctx);  // rebuild the CSR if served updates changed the graph
 void free_serve(abcore_ctx *ctx);
 
 static inline int64_t cnt_ge(const std::vector<int64_t> &t, int32_t thr) {

@@ -31,49 +31,10 @@ constexpr int INIT_THREADS = 256;
 constexpr int STREAM_THREADS = 256;
 
 __global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
-    const int64_t P = (int64_t)a.pU + a.pV;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     LaneStats ls;
     unsigned long long probes = 0, inits = 0;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < P; b += stride) {
-        const int64_t i = b + threadIdx.x;
-        bool viol = false;
-        int32_t x = 0;
-        int nch = 0;
-        if (i < P) {
-            x = i < a.pU ? (int32_t)i : (int32_t)(a.nU + (i - a.pU));
-            const bool upper = x < a.nU;
-            const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
-            int len;
-            if (upper ? a.searchU : a.searchV) {
-                const int32_t bound = upper ? a.nU + a.pV : a.pU;
-                if (e == s) {
-                    len = 0;
-                } else if (__ldg(&a.adj[e - 1]) < bound) {
-                    len = (int)(e - s);
-                    probes++;
-                } else {
-                    int64_t lo = s, hi = e - 1;  // adj[hi] >= bound
-                    probes++;
-                    while (lo < hi) {
-                        const int64_t mid = (lo + hi) >> 1;
-                        probes++;
-                        if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    len = (int)(lo - s);
-                }
-            } else {
-                len = (int)(e - s);
-            }
-            a.cp[x] = make_int2(len, len);
-            inits++;
-            const int32_t thr = upper ? a.thrU : a.thrV;
-            viol = len < thr;
-            nch = abc::chunks_of(len, a.chunk);
-        }
-        abc::warp_push(a, viol, x, nch, ls);
-    }
+    abc::init_range(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls,
+                    probes, inits);
     unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)inits);
     unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)probes);
     unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
@@ -84,75 +45,18 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
     }
 }
 
-// Stream adjacency slices of initial violators; entries landing on candidates decrement them.
-// Slice A = [sa, ea) holds V rows (entries are U ids), slice B = [sb, eb) holds U rows.
-__device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool from_upper, bool valid,
-                                             LaneStats &ls) {
-    bool push = false;
-    int nch = 0;
-    if (valid) {
-        int32_t thr;
-        if (abc::cand_of(a, y, from_upper, thr) && thr > 0) {
-            const int old = atomicSub(&a.cp[y].x, 1);
-            ls.decs++;
-            if (old == thr) {
-                push = true;
-                nch = abc::chunks_of(abc::row_len_of(a, y), a.chunk);
-            }
-        }
-    }
-    abc::warp_push(a, push, y, nch, ls);
-}
-
 __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t sa, int64_t ea, int64_t sb,
                                                            int64_t eb) {
     LaneStats ls;
     unsigned long long ents = 0;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int sl = 0; sl < 2; ++sl) {
-        const int64_t s = sl == 0 ? sa : sb, e = sl == 0 ? ea : eb;
-        if (e <= s) continue;
-        const bool from_upper = sl == 1;
-        const int64_t a0 = min((s + 3) & ~(int64_t)3, e);
-        const int64_t a1 = max(e & ~(int64_t)3, a0);
-        // unaligned head and tail, scalar
-        {
-            const int64_t nh = (a0 - s) + (e - a1);
-            for (int64_t b = 0; b < nh; b += nthreads) {
-                const int64_t i = b + tid;
-                const bool valid = i < nh;
-                int32_t y = 0;
-                if (valid) {
-                    const int64_t pos = i < (a0 - s) ? s + i : a1 + (i - (a0 - s));
-                    y = __ldg(&a.adj[pos]);
-                    ents++;
-                }
-                stream_entry(a, y, from_upper, valid, ls);
-            }
-        }
-        const int64_t nv = (a1 - a0) >> 2;
-        const int4 *v4 = reinterpret_cast<const int4 *>(a.adj + a0);
-        for (int64_t b = 0; b < nv; b += nthreads) {
-            const int64_t i = b + tid;
-            const bool valid = i < nv;
-            int4 q = make_int4(0, 0, 0, 0);
-            if (valid) {
-                q = __ldg(&v4[i]);
-                ents += 4;
-            }
-            stream_entry(a, q.x, from_upper, valid, ls);
-            stream_entry(a, q.y, from_upper, valid, ls);
-            stream_entry(a, q.z, from_upper, valid, ls);
-            stream_entry(a, q.w, from_upper, valid, ls);
-        }
-    }
+    abc::stream_range(a, sa, ea, sb, eb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (int64_t)gridDim.x * blockDim.x, ls, ents);
     unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)ents);
     unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.decs);
     unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
     if ((threadIdx.x & 31) == 0) {
         if (v0) atomicAdd(&a.ctl->st[ST_STREAM], v0);
-        if (v1) atomicAdd(&a.ctl->st[ST_DECS], v1);
+        if (v1) atomicAdd(&a.ctl->st[ST_SDECS], v1);
         if (v2) atomicAdd(&a.ctl->st[ST_PUSHES], v2);
     }
 }
@@ -214,7 +118,9 @@ int peel_prepare(abcore_ctx *ctx) {
     PeelWork &w = ctx->w;
     const Graph &g = ctx->g;
     const int64_t n = g.n();
-    const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024;
+    // every vertex is queued at most once, as ceil(row / chunk) items; idle warps may also hold
+    // one ticket batch each beyond the last item
+    const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 + (int64_t)ctx->num_sms * 64 * 32;
     if (w.n == n && w.qcap >= qcap && w.cp) return ABCORE_OK;
     free_peel(ctx);
     ABC_TRY(ctx->alloc(&w.cp, (size_t)std::max<int64_t>(n, 1), "peel counts"));
@@ -240,7 +146,14 @@ void free_peel(abcore_ctx *ctx) {
     ctx->release(w.stage);
     if (w.ctl_host) cudaFreeHost(w.ctl_host);
     w.ctl_host = nullptr;
-    for (int i = 0; i < CTL_RING; ++i) w.pending[i] = false;
+    for (int i = 0; i < CTL_RING; ++i) {
+        w.pending[i] = false;
+        for (int k = 0; k < 4; ++k)
+            if (w.ev[i][k]) {
+                cudaEventDestroy(w.ev[i][k]);
+                w.ev[i][k] = nullptr;
+            }
+    }
     w.last = -1;
     w.n = w.qcap = 0;
 }
@@ -306,20 +219,34 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.mask_u = d_mask_u;
     a.mask_v = d_mask_v;
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
-    a.emit = scatter ? 2 : 1;
+    a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
+    a.skip_zero = 1;
 
+    SlotInfo &si = w.info[slot];
+    si = SlotInfo{};
+    si.cands = P;
+    si.n = n;
+    si.emit = a.emit;
+    si.timed = ctx->prm.timing != 0;
+    if (si.timed)
+        for (int k = 0; k < 4; ++k)
+            if (!w.ev[slot][k]) ABC_CU(cudaEventCreate(&w.ev[slot][k]));
     if (w.q_dirty) {
         ABC_CU(cudaMemsetAsync(w.q, 0xff, sizeof(unsigned long long) * (size_t)w.qcap, ctx->stream));
         w.q_dirty = false;
     }
     ABC_CU(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), ctx->stream));
-    if (scatter) {
+    if (a.emit == 2) {
         if (nU) ABC_CU(cudaMemsetAsync(d_mask_u, 0, (size_t)nU, ctx->stream));
         if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
     }
+    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
     if (P > 0) {
         const int64_t gi = std::min<int64_t>((P + INIT_THREADS - 1) / INIT_THREADS, (int64_t)ctx->num_sms * 32);
         k_init<<<(unsigned)std::max<int64_t>(gi, 1), INIT_THREADS, 0, ctx->stream>>>(a);
+        si.has_init = true;
+        ctx->stats.launches++;
+        if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][1], ctx->stream));
         // Rows of the initial violators are contiguous: U violators [pU, nU) own
         // adj[off[pU], off[nU]) = [edgesU_ge(alpha), m), V violators [nU+pV, n) own
         // adj[m + edgesV_ge(beta), 2m). Slice A (V rows) feeds U counts, slice B (U rows) V counts.
@@ -337,15 +264,19 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             const int64_t gs = std::min<int64_t>((work + STREAM_THREADS - 1) / STREAM_THREADS,
                                                  (int64_t)ctx->num_sms * 16);
             k_stream<<<(unsigned)std::max<int64_t>(gs, 1), STREAM_THREADS, 0, ctx->stream>>>(a, sa, ea, sb, eb);
+            si.has_stream = true;
+            ctx->stats.launches++;
         }
     }
     if (ctx->prm.debug_stall_slots > 0) k_stall<<<1, 1, 0, ctx->stream>>>(ctl, w.qcap, ctx->prm.debug_stall_slots);
+    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][2], ctx->stream));
     k_cascade<<<blocks, 256, 0, ctx->stream>>>(a);
+    ctx->stats.launches++;
+    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
     ABC_CU(cudaGetLastError());
     ABC_CU(cudaMemcpyAsync(w.ctl_host + slot, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, ctx->stream));
     w.pending[slot] = true;
     w.last = slot;
-    ctx->stats.candidates = P;
     ctx->stats.mode = mode;
     ctx->stats.grid_blocks = blocks;
     ctx->pending_async = true;
@@ -360,23 +291,44 @@ int peel_finish(abcore_ctx *ctx) {
     ctx->pending_async = false;
     ABC_CU(cudaStreamSynchronize(ctx->stream));
     PeelWork &w = ctx->w;
+    abcore_stats &s = ctx->stats;
     int first_err = 0;
     for (int i = 0; i < CTL_RING; ++i) {
         if (!w.pending[i]) continue;
         w.pending[i] = false;
-        if (w.ctl_host[i].err != 0 && first_err == 0) first_err = w.ctl_host[i].err;
-    }
-    if (w.last >= 0) {
-        const PeelCtl &c = w.ctl_host[w.last];
-        abcore_stats &s = ctx->stats;
-        s.init_vertices = (int64_t)c.st[ST_INIT];
-        s.search_probes = (int64_t)c.st[ST_PROBES];
-        s.stream_entries = (int64_t)c.st[ST_STREAM];
-        s.entries = (int64_t)c.st[ST_ENTRIES];
-        s.decrements = (int64_t)c.st[ST_DECS];
-        s.pushes = (int64_t)c.st[ST_PUSHES];
-        s.items = (int64_t)c.st[ST_ITEMS];
-        s.steps = (int64_t)c.st[ST_STEPS];
+        const PeelCtl &c = w.ctl_host[i];
+        const SlotInfo &si = w.info[i];
+        if (c.err != 0 && first_err == 0) first_err = c.err;
+        s.peels++;
+        s.candidates += si.cands;
+        s.init_vertices += (int64_t)c.st[ST_INIT];
+        s.search_probes += (int64_t)c.st[ST_PROBES];
+        s.stream_entries += (int64_t)c.st[ST_STREAM];
+        s.entries += (int64_t)c.st[ST_ENTRIES];
+        s.decrements += (int64_t)c.st[ST_DECS] + (int64_t)c.st[ST_SDECS];
+        s.stream_decrements += (int64_t)c.st[ST_SDECS];
+        s.pushes += (int64_t)c.st[ST_PUSHES];
+        s.items += (int64_t)c.st[ST_ITEMS];
+        if (si.emit == 1) s.emit_gathered += si.n;
+        if (si.emit == 2) {
+            s.emit_scattered += si.cands;
+            s.mask_zeroed += si.n;
+        }
+        if (si.timed) {
+            float ms = 0.f;
+            if (si.has_init && cudaEventElapsedTime(&ms, w.ev[i][0], w.ev[i][1]) == cudaSuccess) {
+                s.kernel_ms[ABCORE_K_INIT] += ms;
+                s.kernel_launches[ABCORE_K_INIT]++;
+            }
+            if (si.has_stream && cudaEventElapsedTime(&ms, w.ev[i][1], w.ev[i][2]) == cudaSuccess) {
+                s.kernel_ms[ABCORE_K_STREAM] += ms;
+                s.kernel_launches[ABCORE_K_STREAM]++;
+            }
+            if (cudaEventElapsedTime(&ms, w.ev[i][2], w.ev[i][3]) == cudaSuccess) {
+                s.kernel_ms[ABCORE_K_CASCADE] += ms;
+                s.kernel_launches[ABCORE_K_CASCADE]++;
+            }
+        }
     }
     if (first_err != 0) {
         w.q_dirty = true;

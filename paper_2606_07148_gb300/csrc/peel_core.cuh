@@ -52,7 +52,10 @@ __device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t 
     if (pm == 0) return;
     const int lane = threadIdx.x & 31;
     if (!want) nch = 0;
-    else ls.pushes++;
+    else {
+        ls.pushes++;
+        if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+    }
     const int incl = warp_incl_scan(nch);
     const int total = __shfl_sync(ABC_FULL, incl, 31);
     if (total == 0) return;
@@ -70,42 +73,28 @@ __device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t 
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
 
-// Warp-collective: process queue slots [h, h + k), k <= 32.
-__device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long h, int k, WarpSmem &sm,
-                                              LaneStats &ls, unsigned long long deadline) {
+// Warp-collective: process the items held by the lanes (`it` == EMPTY: none), spreading the
+// row chunks' entries evenly over the lanes (warp-level load balancing over an exclusive scan).
+__device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long it, WarpSmem &sm,
+                                              LaneStats &ls) {
     const int lane = threadIdx.x & 31;
     long long start = 0;
     int len = 0, upper = 0;
-    if (lane < k && h + lane < (unsigned long long)a.qcap) {
-        unsigned long long *slot = &a.q[h + lane];
-        unsigned long long it = ld_relaxed(slot);
-        while (it == EMPTY) {
-            if (now_ns() > deadline) {
-                set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
-                break;
-            }
-            __nanosleep(32);
-            it = ld_relaxed(slot);
-        }
-        if (it != EMPTY) {
-            st_relaxed(slot, EMPTY);
-            const int32_t x = (int32_t)(it >> 32);
-            const int c = (int)(it & 0xffffffffu);
-            const int rl = row_len_of(a, x);
-            start = __ldg(&a.off[x]) + (long long)c * a.chunk;
-            len = min(a.chunk, rl - c * a.chunk);
-            if (len < 0) len = 0;
-            upper = x < a.nU;
-            ls.items++;
-        }
+    if (it != EMPTY) {
+        const int32_t x = (int32_t)(it >> 32);
+        const int c = (int)(it & 0xffffffffu);
+        const int rl = row_len_of(a, x);
+        start = __ldg(&a.off[x]) + (long long)c * a.chunk;
+        len = min(a.chunk, rl - c * a.chunk);
+        if (len < 0) len = 0;
+        upper = x < a.nU;
+        ls.items++;
     }
     const int incl = warp_incl_scan(len);
     const int L = __shfl_sync(ABC_FULL, incl, 31);
-    if (lane < MAX_GRAB) {
-        sm.start[lane] = start;
-        sm.excl[lane] = incl - len;
-        sm.upper[lane] = upper;
-    }
+    sm.start[lane] = start;
+    sm.excl[lane] = incl - len;
+    sm.upper[lane] = upper;
     __syncwarp();
     int j = 0;
     for (int b = 0; b < L; b += 32) {
@@ -114,12 +103,12 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
         int32_t y = 0;
         int nch = 0;
         if (e < L) {
-            while (j + 1 < k && sm.excl[j + 1] <= e) ++j;
+            while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
             const long long pos = sm.start[j] + (e - sm.excl[j]);
             y = __ldg(&a.adj[pos]);
             ls.entries++;
             int32_t thr;
-            if (cand_of(a, y, sm.upper[j] != 0, thr) && thr > 0) {
+            if (cand_of(a, y, sm.upper[j] != 0, thr) && (thr > 0 || !a.skip_zero)) {
                 const int old = atomicSub(&a.cp[y].x, 1);
                 ls.decs++;
                 if (old == thr) {
@@ -134,57 +123,197 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
 }
 
 // Warp-collective cascade loop: returns 1 when the queue drained, 0 on error.
+//
+// Work is handed out by ticket: lane 0 takes k consecutive slot numbers with one atomicAdd on
+// `head` (k grows with the visible backlog), and lane l owns slot base + l. Pushers fill slots
+// in reservation order, so a ticket below `tail` is filled soon. Items are processed as soon as
+// any lane's slot is filled; lanes still waiting keep their tickets (holding items while
+// waiting could starve the very pushes that fill the remaining slots). When done == tail
+// nothing is in flight, so nothing can be queued any more: every ticket at or above tail will
+// never be filled and its holder leaves. (done is read before tail; both only grow and
+// done <= tail, so equality at those two reads proves the queue drained.)
 __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, LaneStats &ls, int grab_div) {
     const int lane = threadIdx.x & 31;
     unsigned long long idle_since = now_ns(), last_done = ~0ull;
+    int st = 2;  // this lane's ticket: 0 waiting, 2 none
+    unsigned long long my = 0;
+    unsigned sleep_ns = 32;
     for (;;) {
-        int state = 2;  // 0 work, 1 finished, 2 retry, 3 error
-        unsigned long long h = 0;
-        int k = 0;
-        if (lane == 0) {
-            const unsigned long long head = ld_relaxed(&a.ctl->head);
-            const unsigned long long tail = ld_relaxed(&a.ctl->tail);
-            if (head < tail) {
-                unsigned long long avail = tail - head;
-                unsigned long long kk = avail / (unsigned long long)grab_div;
-                if (kk < 1) kk = 1;
-                if (kk > MAX_GRAB) kk = MAX_GRAB;
-                if (atomicCAS(&a.ctl->head, head, head + kk) == head) {
-                    h = head;
-                    k = (int)kk;
-                    state = 0;
+        if (__ballot_sync(ABC_FULL, st == 0) == 0) {  // no ticket held: take new ones
+            unsigned long long base = 0;
+            int k = 1;
+            if (lane == 0) {
+                const unsigned long long t = ld_relaxed(&a.ctl->tail);
+                const unsigned long long h = ld_relaxed(&a.ctl->head);
+                if (t > h) {
+                    const unsigned long long kk = (t - h) / (unsigned long long)grab_div;
+                    k = (int)(kk < 1 ? 1 : (kk > MAX_GRAB ? MAX_GRAB : kk));
                 }
-            } else {
-                const unsigned long long d = ld_acquire(&a.ctl->done);
-                const unsigned long long t2 = ld_acquire(&a.ctl->tail);
-                if (d == t2) state = 1;
-                else if (ld_relaxed_i32(&a.ctl->err) != 0) state = 3;
-                else {
-                    if (d != last_done) {  // the device is making progress: restart the clock
-                        last_done = d;
-                        idle_since = now_ns();
-                    }
-                    if (now_ns() - idle_since > a.timeout_ns) {
-                        set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
-                        state = 3;
-                    } else {
-                        __nanosleep(64);
-                    }
-                }
+                base = atomicAdd(&a.ctl->head, (unsigned long long)k);
+            }
+            base = __shfl_sync(ABC_FULL, base, 0);
+            k = __shfl_sync(ABC_FULL, k, 0);
+            my = base + (unsigned long long)lane;
+            st = (lane < k && my < (unsigned long long)a.qcap) ? 0 : 2;
+        }
+        unsigned long long it = EMPTY;
+        if (st == 0) {
+            it = ld_relaxed(&a.q[my]);
+            if (it != EMPTY) {
+                st_relaxed(&a.q[my], EMPTY);
+                st = 2;
             }
         }
-        state = __shfl_sync(ABC_FULL, state, 0);
-        if (state == 1) return 1;
-        if (state == 3) return 0;
-        if (state == 2) continue;
-        h = __shfl_sync(ABC_FULL, h, 0);
-        k = __shfl_sync(ABC_FULL, k, 0);
-        process_items(a, h, k, sm, ls, now_ns() + a.timeout_ns);
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(&a.ctl->done, (unsigned long long)k);
-        idle_since = now_ns();
-        if (ld_relaxed_i32(&a.ctl->err) != 0) return 0;
+        const unsigned have = __ballot_sync(ABC_FULL, it != EMPTY);
+        if (have != 0) {
+            process_items(a, it, sm, ls);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(&a.ctl->done, (unsigned long long)__popc(have));
+            idle_since = now_ns();
+            sleep_ns = 32;
+            if (ld_relaxed_i32(&a.ctl->err) != 0) return 0;
+            continue;
+        }
+        // nothing arrived: is the queue drained, is there an error, or has it stalled?
+        int verdict = 0;  // 0 keep waiting, 1 drained, 3 error
+        unsigned long long tcur = 0;
+        if (lane == 0) {
+            const unsigned long long d = ld_acquire(&a.ctl->done);
+            tcur = ld_acquire(&a.ctl->tail);
+            if (d == tcur) verdict = 1;
+            else if (ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
+            else if (d != last_done) {  // the device is making progress: restart the clock
+                last_done = d;
+                idle_since = now_ns();
+            } else if (now_ns() - idle_since > a.timeout_ns) {
+                set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
+                verdict = 3;
+            }
+        }
+        verdict = __shfl_sync(ABC_FULL, verdict, 0);
+        if (verdict == 3) return 0;
+        if (verdict == 1) {
+            tcur = __shfl_sync(ABC_FULL, tcur, 0);
+            // a ticket below tail must be filled already (everything reserved was processed,
+            // and only its holder processes it), so every waiting ticket here is >= tail
+            if (st == 0 && my >= tcur) st = 2;
+            if (__ballot_sync(ABC_FULL, st == 0) == 0) return 1;
+            continue;
+        }
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 1024) sleep_ns <<= 1;
+    }
+}
+
+// Candidate counts (the scan phase): thread t of nthreads handles candidates t, t + nthreads, ...
+// Per layer, the count is either the row prefix below the other layer's candidate boundary
+// (binary search in the sorted row) or the full degree (to be corrected by stream_range).
+// Candidates already below their bound are queued. Warp-collective; `t0` is warp-aligned.
+__device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_t nthreads, LaneStats &ls,
+                                           unsigned long long &probes, unsigned long long &inits) {
+    const int64_t P = (int64_t)a.pU + a.pV;
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = t0 - lane; b < P; b += nthreads) {
+        const int64_t i = b + lane;
+        bool viol = false;
+        int32_t x = 0;
+        int nch = 0;
+        if (i < P) {
+            x = i < a.pU ? (int32_t)i : (int32_t)(a.nU + (i - a.pU));
+            const bool upper = x < a.nU;
+            const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
+            int len;
+            if (upper ? a.searchU : a.searchV) {
+                const int32_t bound = upper ? a.nU + a.pV : a.pU;
+                if (e == s) {
+                    len = 0;
+                } else if (__ldg(&a.adj[e - 1]) < bound) {
+                    len = (int)(e - s);
+                    probes++;
+                } else {
+                    int64_t lo = s, hi = e - 1;  // adj[hi] >= bound
+                    probes++;
+                    while (lo < hi) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        probes++;
+                        if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    len = (int)(lo - s);
+                }
+            } else {
+                len = (int)(e - s);
+            }
+            a.cp[x] = make_int2(len, len);
+            inits++;
+            const int32_t thr = upper ? a.thrU : a.thrV;
+            viol = len < thr;
+            nch = chunks_of(len, a.chunk);
+        }
+        warp_push(a, viol, x, nch, ls);
+    }
+}
+
+// One adjacency entry y of an initial violator's row: decrement y if it is a candidate.
+__device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool from_upper, bool valid,
+                                             LaneStats &ls) {
+    bool push = false;
+    int nch = 0;
+    if (valid) {
+        int32_t thr;
+        if (cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero)) {
+            const int old = atomicSub(&a.cp[y].x, 1);
+            ls.decs++;
+            if (old == thr) {
+                push = true;
+                nch = chunks_of(row_len_of(a, y), a.chunk);
+            }
+        }
+    }
+    warp_push(a, push, y, nch, ls);
+}
+
+// Stream the rows of the initial violators (the first peel round): slice A = adj[sa, ea) holds
+// V rows (entries are U ids), slice B = adj[sb, eb) holds U rows. Interior read with 16-byte
+// loads. Warp-collective; `t0` is this thread's index among nthreads (a multiple of 32).
+__device__ __forceinline__ void stream_range(const PeelArgs &a, int64_t sa, int64_t ea, int64_t sb, int64_t eb,
+                                             int64_t t0, int64_t nthreads, LaneStats &ls,
+                                             unsigned long long &ents) {
+    const int lane = threadIdx.x & 31;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int64_t s = sl == 0 ? sa : sb, e = sl == 0 ? ea : eb;
+        if (e <= s) continue;
+        const bool from_upper = sl == 1;
+        const int64_t a0 = min((s + 3) & ~(int64_t)3, e);
+        const int64_t a1 = max(e & ~(int64_t)3, a0);
+        const int64_t nh = (a0 - s) + (e - a1);
+        for (int64_t b = t0 - lane; b < nh; b += nthreads) {
+            const int64_t i = b + lane;
+            const bool valid = i < nh;
+            int32_t y = 0;
+            if (valid) {
+                const int64_t pos = i < (a0 - s) ? s + i : a1 + (i - (a0 - s));
+                y = __ldg(&a.adj[pos]);
+                ents++;
+            }
+            stream_entry(a, y, from_upper, valid, ls);
+        }
+        const int64_t nv = (a1 - a0) >> 2;
+        const int4 *v4 = reinterpret_cast<const int4 *>(a.adj + a0);
+        for (int64_t b = t0 - lane; b < nv; b += nthreads) {
+            const int64_t i = b + lane;
+            const bool valid = i < nv;
+            int4 q = make_int4(0, 0, 0, 0);
+            if (valid) {
+                q = __ldg(&v4[i]);
+                ents += 4;
+            }
+            stream_entry(a, q.x, from_upper, valid, ls);
+            stream_entry(a, q.y, from_upper, valid, ls);
+            stream_entry(a, q.z, from_upper, valid, ls);
+            stream_entry(a, q.w, from_upper, valid, ls);
+        }
     }
 }
 

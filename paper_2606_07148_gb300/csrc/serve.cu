@@ -1,20 +1,834 @@
-// On-the-fly queries and the serving loop. Placeholder entry points.
+// On-the-fly (alpha, beta)-core queries under edge updates (Section 5, GFQ) and the device-resident,
+// continuously batched serving loop.
+//
+// Question answered for update k (Section 3, on-the-fly query problem): apply the insert or delete
+// of e = (u, v), then report whether e lies in the (alpha, beta)-core of the updated graph. The
+// core is vertex-induced, so that is "u and v are both in the core" (the endpoint bits are
+// returned too). Answers follow arrival order exactly, as if requests ran one at a time.
+//
+// Scope of the re-peel. GFQ re-peels the connected component of the update (Section 5). This
+// engine keeps each target core C and its in-core degrees and re-peels a smaller region that
+// still gives exactly the core of the updated graph G':
+//  * delete (u, v) with both in C: the new core lies inside C, so only a cascade inside C,
+//    started at u and v, is needed; a delete with an endpoint outside C changes nothing;
+//  * insert (u, v): the new core contains C, and every new member lies in a connected piece of
+//    G'[V \ C] that touches u or v (a piece away from e would already have joined C in G).
+//    So a BFS from the non-core endpoints through non-core vertices whose degree meets their
+//    bound finds the only region R that can join; R is peeled with C held fixed and its
+//    survivors join C. If both endpoints are in C, nothing can join.
+//
+// Data on the device. The base CSR (internal, degree-ordered ids) is shared and never changes.
+// Each target keeps its own view of the updates -- tombstone bits over base adjacency slots, a
+// list of inserted neighbours per vertex, current degrees -- plus its core mask and in-core
+// counts, so the targets never wait for one another: each target is one block of the serving
+// kernel and applies every update in order to its own view.
+//
+// Requests travel through a ring in pinned, device-mapped host memory; each block polls the
+// published request count, processes requests in sequence, and the block owning a request's
+// target writes its response into a mapped completion ring. The kernel leaves after an idle
+// spell without requests (a bounded wait) and the host relaunches it on the next submit or
+// poll; every other wait is bounded as well and ends in ABCORE_ETIMEDOUT.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "device.cuh"
 #include "internal.h"
 
-struct ServeState {};
+namespace {
 
-int query_edge(abcore_ctx *ctx, int32_t, int32_t, int, int32_t, int32_t, uint8_t *) {
-    return ctx->fail(ABCORE_EINVAL, "query_edge: not available");
+constexpr int SERVE_THREADS = 256;
+constexpr int SERVE_WARPS = SERVE_THREADS / 32;
+
+struct DNode {
+    int32_t y;      // neighbour (internal id)
+    int32_t next;   // next node of this vertex's list, -1 = end
+    int32_t alive;  // 0 once the edge is deleted again
+    int32_t pad;
+};
+
+struct TargetDev {
+    int32_t alpha, beta;
+    uint8_t *M;        // [n] core membership
+    int32_t *cnt;      // [n] members: in-core degree; region vertices: region count
+    int32_t *deg;      // [n] degree in the current graph
+    uint32_t *tomb;    // [ceil(2m / 32)] deleted base adjacency slots
+    int32_t *dhead;    // [n] inserted-neighbour list heads (-1 = none)
+    DNode *dpool;      // [dcap]
+    int32_t *dcount;   // nodes used
+    int32_t dcap;
+    int32_t *mark;     // [n] epoch tags for region / cascade membership
+    int32_t *q;        // [2n] scratch queue (a region, then the region vertices it peels)
+    int32_t *epoch;    // persisted epoch counter
+};
+
+struct ServeArgs {
+    const int64_t *off;
+    const int32_t *adj;
+    const int32_t *old2new;
+    int32_t nU, nV;
+    TargetDev *targets;
+    int32_t ntargets;
+    const abcore_req *req;              // mapped host ring
+    abcore_resp *resp;                  // mapped host ring
+    unsigned long long *resp_seq;       // mapped: seq + 1 once resp[slot] is valid
+    const unsigned long long *submitted;  // mapped: requests published by the host
+    const int *stop;                    // mapped: host asks the loop to leave once idle
+    unsigned long long *progress_host;  // mapped: requests processed, per target
+    unsigned long long *progress_dev;   // device: requests processed, per target
+    unsigned long long *exit_at;        // device: ~0, or the request count every block stops at
+    int *err;                           // device: first error
+    int32_t slots;
+    unsigned long long idle_ns, timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
-int serve_start(abcore_ctx *ctx, const int32_t *, const int32_t *, int32_t, int32_t) {
-    return ctx->fail(ABCORE_EINVAL, "serve: not available");
+__device__ __forceinline__ int ld_sys_i32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
-int serve_submit(abcore_ctx *ctx, const abcore_req *, int32_t, uint64_t *) {
-    return ctx->fail(ABCORE_EINVAL, "serve: not available");
+__device__ __forceinline__ void st_sys(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-int serve_poll(abcore_ctx *ctx, abcore_resp *, int32_t, int32_t *n_out) {
+
+__device__ __forceinline__ bool tomb_get(const uint32_t *t, int64_t p) { return (t[p >> 5] >> (p & 31)) & 1u; }
+__device__ __forceinline__ void tomb_set(uint32_t *t, int64_t p, bool on) {
+    if (on) atomicOr(&t[p >> 5], 1u << (p & 31));
+    else atomicAnd(&t[p >> 5], ~(1u << (p & 31)));
+}
+
+// Block-collective search of `key` in the ascending row adj[s, e): its position or -1.
+__device__ int64_t cta_find(const int32_t *adj, int64_t s, int64_t e, int32_t key) {
+    __shared__ int64_t lo_s, hi_s, found_s;
+    __shared__ int32_t sval[SERVE_THREADS];
+    if (threadIdx.x == 0) {
+        lo_s = s;
+        hi_s = e;
+        found_s = -1;
+    }
+    __syncthreads();
+    for (;;) {
+        const int64_t lo = lo_s, hi = hi_s, len = hi - lo;
+        if (len <= (int64_t)SERVE_THREADS * 4) {
+            for (int64_t p = lo + threadIdx.x; p < hi; p += SERVE_THREADS)
+                if (__ldg(&adj[p]) == key) found_s = p;
+            __syncthreads();
+            break;
+        }
+        const int64_t pos = lo + (len * threadIdx.x) / SERVE_THREADS;
+        sval[threadIdx.x] = __ldg(&adj[pos]);
+        __syncthreads();
+        const int32_t v = sval[threadIdx.x];
+        if (threadIdx.x == 0 && v > key) hi_s = lo;  // key below the row: empty interval
+        if (v <= key && (threadIdx.x == SERVE_THREADS - 1 || sval[threadIdx.x + 1] > key)) {
+            lo_s = pos;
+            hi_s = threadIdx.x == SERVE_THREADS - 1 ? hi : lo + (len * (threadIdx.x + 1)) / SERVE_THREADS;
+        }
+        __syncthreads();
+    }
+    const int64_t r = found_s;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int32_t thr_of(const ServeArgs &A, const TargetDev &S, int32_t z) {
+    return z < A.nU ? S.alpha : S.beta;
+}
+
+// Visit the current neighbours of w: base row minus tombstones, plus live inserted neighbours.
+// Warp-collective: lanes stride the base row; the inserted list is walked by every lane in step.
+template <class F>
+__device__ __forceinline__ void for_neighbours(const ServeArgs &A, const TargetDev &S, int32_t w, F f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = __ldg(&A.off[w]), e = __ldg(&A.off[w + 1]);
+    for (int64_t p = s + lane; p < e; p += 32)
+        if (!tomb_get(S.tomb, p)) f(__ldg(&A.adj[p]));
+    for (int32_t nd = S.dhead[w]; nd >= 0;) {
+        const DNode d = S.dpool[nd];
+        if (lane == 0 && d.alive) f(d.y);
+        nd = d.next;
+    }
+}
+
+// Process queue entries level by level: each warp takes entries of the current level,
+// `body(w)` may push new entries through `push`. Block-collective.
+struct BlockQueue {
+    int32_t *q;
+    int *tail;  // shared
+};
+
+__device__ __forceinline__ void bq_push(BlockQueue &Q, int32_t z) { Q.q[atomicAdd(Q.tail, 1)] = z; }
+
+// Cascade inside the core after a delete: members whose in-core count fell below their bound
+// leave, lowering their member neighbours' counts (queued on the exact crossing).
+__device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y) {
+    __shared__ int tail;
+    BlockQueue Q{S.q, &tail};
+    if (threadIdx.x == 0) {
+        tail = 0;
+        const int32_t cx = --S.cnt[x], cy = --S.cnt[y];
+        if (cx < thr_of(A, S, x)) { S.M[x] = 0; Q.q[tail++] = x; }
+        if (cy < thr_of(A, S, y)) { S.M[y] = 0; Q.q[tail++] = y; }
+    }
+    __syncthreads();
+    int head = 0;
+    const int warp = threadIdx.x >> 5;
+    while (head < tail) {
+        const int end = tail;
+        __syncthreads();
+        for (int i = head + warp; i < end; i += SERVE_WARPS) {
+            const int32_t w = S.q[i];
+            for_neighbours(A, S, w, [&](int32_t z) {
+                if (S.M[z]) {
+                    const int old = atomicSub(&S.cnt[z], 1);
+                    if (old == thr_of(A, S, z)) {
+                        S.M[z] = 0;
+                        bq_push(Q, z);
+                    }
+                }
+            });
+        }
+        __syncthreads();
+        head = end;
+    }
+}
+
+// Region growth and peel after an insert with an endpoint outside the core.
+__device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y, int32_t ep) {
+    __shared__ int tail, abort_flag;
+    BlockQueue Q{S.q, &tail};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        tail = 0;
+        abort_flag = 0;
+        const int32_t ends[2] = {x, y};
+        for (int i = 0; i < 2; ++i) {
+            const int32_t z = ends[i];
+            if (S.M[z]) continue;
+            if (S.deg[z] < thr_of(A, S, z)) abort_flag = 1;  // z can never join: nothing changes
+            else if (S.mark[z] != ep) {
+                S.mark[z] = ep;
+                Q.q[tail++] = z;
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_flag) return;
+    // grow R: non-core vertices meeting their bound on degree, connected to the seeds
+    int head = 0;
+    while (head < tail) {
+        const int end = tail;
+        __syncthreads();
+        for (int i = head + warp; i < end; i += SERVE_WARPS) {
+            const int32_t w = S.q[i];
+            for_neighbours(A, S, w, [&](int32_t z) {
+                if (!S.M[z] && S.deg[z] >= thr_of(A, S, z)) {
+                    const int old = atomicExch(&S.mark[z], ep);
+                    if (old != ep) bq_push(Q, z);
+                }
+            });
+        }
+        __syncthreads();
+        head = end;
+    }
+    const int R = tail;
+    // region counts: neighbours in C or in R
+    for (int i = warp; i < R; i += SERVE_WARPS) {
+        const int32_t w = S.q[i];
+        int c = 0;
+        for_neighbours(A, S, w, [&](int32_t z) { c += (S.M[z] || S.mark[z] == ep) ? 1 : 0; });
+        for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(ABC_FULL, c, d);
+        if (lane == 0) S.cnt[w] = c;
+    }
+    __syncthreads();
+    // peel R with C fixed: removed region vertices get tag ep + 1
+    if (threadIdx.x == 0) tail = R;
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += SERVE_THREADS) {
+        const int32_t w = S.q[i];
+        if (S.cnt[w] < thr_of(A, S, w)) {
+            S.mark[w] = ep + 1;
+            bq_push(Q, w);
+        }
+    }
+    __syncthreads();
+    head = R;
+    while (head < tail) {
+        const int end = tail;
+        __syncthreads();
+        for (int i = head + warp; i < end; i += SERVE_WARPS) {
+            const int32_t w = S.q[i];
+            for_neighbours(A, S, w, [&](int32_t z) {
+                if (S.mark[z] == ep) {
+                    const int old = atomicSub(&S.cnt[z], 1);
+                    if (old == thr_of(A, S, z)) {
+                        S.mark[z] = ep + 1;
+                        bq_push(Q, z);
+                    }
+                }
+            });
+        }
+        __syncthreads();
+        head = end;
+    }
+    // survivors join C; their old-core neighbours gain one in-core neighbour per edge
+    for (int i = warp; i < R; i += SERVE_WARPS) {
+        const int32_t w = S.q[i];
+        if (S.mark[w] != ep) continue;
+        for_neighbours(A, S, w, [&](int32_t z) {
+            if (S.M[z] && S.mark[z] != ep) atomicAdd(&S.cnt[z], 1);
+        });
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += SERVE_THREADS) {
+        const int32_t w = S.q[i];
+        if (S.mark[w] == ep) S.M[w] = 1;
+    }
+    __syncthreads();
+}
+
+// One update against one target's view. Returns the status; *bits = (u in C) | (v in C) << 1.
+__device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t x, int32_t y, int32_t ep,
+                              int *bits) {
+    __shared__ int status_s;
+    __shared__ int32_t dnode_s;
+    const int64_t px = cta_find(A.adj, __ldg(&A.off[x]), __ldg(&A.off[x + 1]), y);
+    int64_t py = -1;
+    if (px >= 0) py = cta_find(A.adj, __ldg(&A.off[y]), __ldg(&A.off[y + 1]), x);
+    if (threadIdx.x == 0) {
+        dnode_s = -1;
+        bool present;
+        if (px >= 0) {
+            present = !tomb_get(S.tomb, px);
+        } else {
+            present = false;
+            for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next)
+                if (S.dpool[nd].y == y && S.dpool[nd].alive) {
+                    present = true;
+                    dnode_s = nd;
+                    break;
+                }
+        }
+        int st = ABCORE_OK;
+        if (op == ABCORE_INSERT && present) st = ABCORE_EEXIST;
+        if (op == ABCORE_DELETE && !present) st = ABCORE_ENOENT;
+        status_s = st;
+        if (st == ABCORE_OK) {
+            if (op == ABCORE_INSERT) {
+                if (px >= 0) {
+                    tomb_set(S.tomb, px, false);
+                    tomb_set(S.tomb, py, false);
+                } else {
+                    const int32_t a = atomicAdd(S.dcount, 2);
+                    if (a + 2 > S.dcap) {
+                        abc::set_error(A.err, ABCORE_ENOMEM);
+                        status_s = ABCORE_ENOMEM;
+                    } else {
+                        S.dpool[a] = DNode{y, S.dhead[x], 1, 0};
+                        S.dhead[x] = a;
+                        S.dpool[a + 1] = DNode{x, S.dhead[y], 1, 0};
+                        S.dhead[y] = a + 1;
+                    }
+                }
+                if (status_s == ABCORE_OK) {
+                    S.deg[x]++;
+                    S.deg[y]++;
+                }
+            } else {
+                if (px >= 0) {
+                    tomb_set(S.tomb, px, true);
+                    tomb_set(S.tomb, py, true);
+                } else {
+                    S.dpool[dnode_s].alive = 0;
+                    for (int32_t nd = S.dhead[y]; nd >= 0; nd = S.dpool[nd].next)
+                        if (S.dpool[nd].y == x && S.dpool[nd].alive) {
+                            S.dpool[nd].alive = 0;
+                            break;
+                        }
+                }
+                S.deg[x]--;
+                S.deg[y]--;
+            }
+        }
+    }
+    __syncthreads();
+    const int st = status_s;
+    if (st == ABCORE_OK) {
+        const bool mx = S.M[x], my = S.M[y];
+        __syncthreads();
+        if (op == ABCORE_INSERT) {
+            if (mx && my) {
+                if (threadIdx.x == 0) {
+                    S.cnt[x]++;
+                    S.cnt[y]++;
+                }
+            } else {
+                insert_region(A, S, x, y, ep);
+            }
+        } else if (mx && my) {
+            delete_cascade(A, S, x, y);
+        }
+    }
+    __syncthreads();
+    *bits = (S.M[x] ? 1 : 0) | (S.M[y] ? 2 : 0);
+    __syncthreads();
+    return st;
+}
+
+__global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
+    __shared__ int state_s;  // 0 work, 1 leave
+    __shared__ abcore_req r_s;
+    TargetDev S = A.targets[blockIdx.x];
+    const int t = blockIdx.x;
+    unsigned long long k = A.progress_dev[t];
+    int32_t ep = *S.epoch;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            state_s = 0;
+            const unsigned long long t0 = abc::now_ns();
+            unsigned sl = 64;
+            for (;;) {
+                const unsigned long long ex = abc::ld_relaxed(A.exit_at);
+                if (k >= ex) {  // the loop is closing at request count ex
+                    state_s = 1;
+                    break;
+                }
+                const unsigned long long sub = ld_sys(A.submitted);
+                if (k < sub) break;
+                if (abc::ld_relaxed_i32(A.err)) {
+                    state_s = 1;
+                    break;
+                }
+                if (ld_sys_i32(A.stop) || abc::now_ns() - t0 > A.idle_ns) {
+                    // stop request or idle spell: close the loop for every block at count `sub`,
+                    // so no block handles a request the others skip; the host relaunches later
+                    atomicCAS(A.exit_at, ~0ull, sub);
+                    continue;
+                }
+                __nanosleep(sl);
+                if (sl < 2048) sl <<= 1;
+            }
+            if (state_s == 0) {
+                const abcore_req *rq = A.req + (k % (unsigned long long)A.slots);
+                volatile const int32_t *w = reinterpret_cast<volatile const int32_t *>(rq);
+                r_s.op = w[0];
+                r_s.u = w[1];
+                r_s.v = w[2];
+                r_s.target = w[3];
+                r_s.tag = *reinterpret_cast<volatile const uint64_t *>(&rq->tag);
+            }
+        }
+        __syncthreads();
+        if (state_s != 0) break;
+        const abcore_req r = r_s;
+        const int32_t x = __ldg(&A.old2new[r.u]);
+        const int32_t y = __ldg(&A.old2new[A.nU + r.v]);
+        ep += 2;
+        int bits = 0;
+        const int st = process_update(A, S, r.op, x, y, ep, &bits);
+        if (threadIdx.x == 0) {
+            if (r.target == t) {
+                abcore_resp *o = A.resp + (k % (unsigned long long)A.slots);
+                o->seq = k;
+                o->tag = r.tag;
+                o->status = st;
+                o->u_in = (uint8_t)(bits & 1);
+                o->v_in = (uint8_t)((bits >> 1) & 1);
+                o->in_core = (uint8_t)(bits == 3);
+                o->pad = 0;
+                __threadfence_system();
+                st_sys(&A.resp_seq[k % (unsigned long long)A.slots], k + 1);
+            }
+            A.progress_dev[t] = k + 1;
+            __threadfence_system();
+            st_sys(&A.progress_host[t], k + 1);
+        }
+        ++k;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *S.epoch = ep;
+}
+
+// Target state from a fresh peel: membership, in-core counts, degrees, empty update view.
+__global__ void k_target_init(const int64_t *off, const int2 *cp, int32_t nU, int32_t nV, int32_t pU, int32_t pV,
+                              int32_t alpha, int32_t beta, TargetDev S) {
+    const int64_t n = (int64_t)nU + nV;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        bool alive;
+        int c = 0;
+        if (x < nU) alive = x < pU && (c = cp[x].x) >= alpha;
+        else alive = x - nU < pV && (c = cp[x].x) >= beta;
+        S.M[x] = alive ? 1 : 0;
+        S.cnt[x] = alive ? c : 0;
+        S.deg[x] = (int32_t)(off[x + 1] - off[x]);
+        S.dhead[x] = -1;
+        S.mark[x] = 0;
+    }
+}
+
+// Edges of the current graph (view of target 0) in caller ids, for rebuilding the CSR.
+__global__ void k_collect_edges(const int64_t *off, const int32_t *adj, const int32_t *new2old, int32_t nU,
+                                TargetDev S, int32_t *eu, int32_t *ev, unsigned long long *count) {
+    const int64_t m = off[nU];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        if (tomb_get(S.tomb, p)) continue;
+        // row of p: binary search in off[0..nU]
+        int32_t lo = 0, hi = nU - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const unsigned long long i = atomicAdd(count, 1ull);
+        eu[i] = new2old[lo];
+        ev[i] = new2old[adj[p]];
+    }
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nU; x += (int64_t)gridDim.x * blockDim.x) {
+        for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next) {
+            const DNode d = S.dpool[nd];
+            if (!d.alive) continue;
+            const unsigned long long i = atomicAdd(count, 1ull);
+            eu[i] = new2old[x];
+            ev[i] = new2old[d.y];
+        }
+    }
+}
+
+}  // namespace
+
+struct ServeState {
+    std::vector<int32_t> alphas, betas;
+    std::vector<TargetDev> tdev;
+    TargetDev *d_targets = nullptr;
+    std::vector<void *> bufs;  // device buffers to release
+    int32_t slots = 0;
+    // mapped host memory
+    abcore_req *h_req = nullptr;
+    abcore_resp *h_resp = nullptr;
+    unsigned long long *h_resp_seq = nullptr;
+    unsigned long long *h_ctl = nullptr;  // [0] submitted, [8] stop (int), [16..] progress per target
+    abcore_req *d_req = nullptr;
+    abcore_resp *d_resp = nullptr;
+    unsigned long long *d_resp_seq = nullptr, *d_ctl = nullptr;
+    unsigned long long *d_progress = nullptr, *d_exit_at = nullptr;
+    int *d_err = nullptr;
+    unsigned long long next_seq = 0, consumed = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t loop_done = nullptr;
+    bool loop_launched = false;
+    bool dirty = false;  // updates applied since the CSR was built
+    int64_t dcap = 0;
+};
+
+static int64_t *ctl_stop_ptr(unsigned long long *ctl) { return (int64_t *)(ctl + 8); }
+
+static bool loop_running(ServeState *s) {
+    if (!s->loop_launched) return false;
+    return cudaEventQuery(s->loop_done) == cudaErrorNotReady;
+}
+
+static unsigned long long min_progress(ServeState *s) {
+    unsigned long long mn = ~0ull;
+    for (size_t t = 0; t < s->alphas.size(); ++t) {
+        const unsigned long long p = __atomic_load_n(&s->h_ctl[16 + t], __ATOMIC_ACQUIRE);
+        mn = std::min(mn, p);
+    }
+    return mn;
+}
+
+static int launch_loop(abcore_ctx *ctx, ServeState *s) {
+    const Graph &g = ctx->g;
+    ServeArgs A{};
+    A.off = g.off;
+    A.adj = g.adj;
+    A.old2new = g.old2new;
+    A.nU = g.nU;
+    A.nV = g.nV;
+    A.targets = s->d_targets;
+    A.ntargets = (int32_t)s->alphas.size();
+    A.req = s->d_req;
+    A.resp = s->d_resp;
+    A.resp_seq = s->d_resp_seq;
+    A.submitted = s->d_ctl;
+    A.stop = (const int *)(s->d_ctl + 8);
+    A.progress_host = s->d_ctl + 16;
+    A.progress_dev = s->d_progress;
+    A.exit_at = s->d_exit_at;
+    A.err = s->d_err;
+    A.slots = s->slots;
+    A.idle_ns = 200ull * 1000000ull;
+    A.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
+    ABC_CU(cudaMemsetAsync(s->d_exit_at, 0xff, sizeof(unsigned long long), s->stream));
+    k_serve<<<A.ntargets, SERVE_THREADS, 0, s->stream>>>(A);
+    ABC_CU(cudaGetLastError());
+    ABC_CU(cudaEventRecord(s->loop_done, s->stream));
+    s->loop_launched = true;
+    ctx->stats.launches++;
+    return ABCORE_OK;
+}
+
+static int check_device_error(abcore_ctx *ctx, ServeState *s) {
+    if (s->loop_launched && !loop_running(s)) {
+        int e = 0;
+        ABC_CU(cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e == ABCORE_ENOMEM) return ctx->fail(ABCORE_ENOMEM, "serve: inserted-edge pool exhausted");
+        if (e) return ctx->fail(e, "serve: device reported error %d", e);
+    }
+    return ABCORE_OK;
+}
+
+static int ensure_loop(abcore_ctx *ctx, ServeState *s) {
+    if (s->next_seq > min_progress(s) && !loop_running(s)) {
+        ABC_TRY(check_device_error(ctx, s));
+        ABC_TRY(launch_loop(ctx, s));
+    }
+    return ABCORE_OK;
+}
+
+static void release_serve(abcore_ctx *ctx, ServeState *s) {
+    if (s->loop_launched) {
+        __atomic_store_n(ctl_stop_ptr(s->h_ctl), (int64_t)1, __ATOMIC_RELEASE);
+        cudaStreamSynchronize(s->stream);
+    }
+    for (void *p : s->bufs) ctx->release(p);
+    s->bufs.clear();
+    ctx->release(s->d_targets);
+    ctx->release(s->d_progress);
+    ctx->release(s->d_exit_at);
+    ctx->release(s->d_err);
+    if (s->h_req) cudaFreeHost(s->h_req);
+    if (s->h_resp) cudaFreeHost(s->h_resp);
+    if (s->h_resp_seq) cudaFreeHost(s->h_resp_seq);
+    if (s->h_ctl) cudaFreeHost(s->h_ctl);
+    s->h_req = nullptr;
+    s->h_resp = nullptr;
+    s->h_resp_seq = nullptr;
+    s->h_ctl = nullptr;
+    if (s->loop_done) cudaEventDestroy(s->loop_done);
+    s->loop_done = nullptr;
+    if (s->stream) cudaStreamDestroy(s->stream);
+    s->stream = nullptr;
+    s->loop_launched = false;
+}
+
+// Rebuild the CSR from the current graph (target 0's view) after updates, so static calls and
+// new targets see the updated graph.
+static int materialize(abcore_ctx *ctx) {
+    ServeState *s = ctx->serve;
+    if (!s || !s->dirty || s->tdev.empty()) return ABCORE_OK;
+    const Graph &g = ctx->g;
+    const int64_t cap = g.m + s->dcap / 2 + 16;
+    int32_t *eu = nullptr, *ev = nullptr;
+    unsigned long long *cnt = nullptr;
+    ABC_TRY(ctx->alloc(&eu, (size_t)cap, "rebuild edges"));
+    int rc = ctx->alloc(&ev, (size_t)cap, "rebuild edges");
+    if (!rc) rc = ctx->alloc(&cnt, 1, "rebuild count");
+    unsigned long long m2 = 0;
+    if (!rc) {
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream);
+        k_collect_edges<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, g.adj, g.new2old, g.nU, s->tdev[0], eu, ev, cnt);
+        cudaMemcpyAsync(&m2, cnt, sizeof(m2), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = ctx->cuda_fail(e, "rebuild");
+    }
+    const int32_t nU = g.nU, nV = g.nV;
+    if (!rc) {
+        release_serve(ctx, s);
+        delete s;
+        ctx->serve = nullptr;
+        free_batch(ctx);
+        free_peel(ctx);
+        rc = build_graph_from_device_edges(ctx, nU, nV, (int64_t)m2, eu, ev);
+    }
+    ctx->release(eu);
+    ctx->release(ev);
+    ctx->release(cnt);
+    return rc;
+}
+
+int serve_materialize(abcore_ctx *ctx) {
+    if (ctx->serve && ctx->serve->loop_launched) ABC_TRY(serve_stop(ctx));  // finish outstanding requests
+    return materialize(ctx);
+}
+
+void free_serve(abcore_ctx *ctx) {
+    if (!ctx->serve) return;
+    release_serve(ctx, ctx->serve);
+    delete ctx->serve;
+    ctx->serve = nullptr;
+}
+
+template <class T>
+static int serve_alloc(abcore_ctx *ctx, ServeState *s, T **p, size_t n, const char *what) {
+    ABC_TRY(ctx->alloc(p, n, what));
+    s->bufs.push_back((void *)*p);
+    return ABCORE_OK;
+}
+
+int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t nt, int32_t slots) {
+    if (ctx->serve) {
+        ABC_TRY(serve_stop(ctx));
+        ABC_TRY(materialize(ctx));
+        free_serve(ctx);
+    }
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    ServeState *s = new ServeState();
+    ctx->serve = s;
+    s->alphas.assign(ta, ta + nt);
+    s->betas.assign(tb, tb + nt);
+    s->slots = slots;
+    s->dcap = 2 * (int64_t)std::max<int32_t>(slots, 1 << 16) + 1024;
+    ABC_CU(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    ABC_CU(cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming));
+    ABC_CU(cudaHostAlloc(&s->h_req, sizeof(abcore_req) * slots, cudaHostAllocMapped));
+    ABC_CU(cudaHostAlloc(&s->h_resp, sizeof(abcore_resp) * slots, cudaHostAllocMapped));
+    ABC_CU(cudaHostAlloc(&s->h_resp_seq, sizeof(unsigned long long) * slots, cudaHostAllocMapped));
+    ABC_CU(cudaHostAlloc(&s->h_ctl, sizeof(unsigned long long) * (16 + nt), cudaHostAllocMapped));
+    memset(s->h_resp_seq, 0, sizeof(unsigned long long) * slots);
+    memset(s->h_ctl, 0, sizeof(unsigned long long) * (16 + nt));
+    ABC_CU(cudaHostGetDevicePointer((void **)&s->d_req, s->h_req, 0));
+    ABC_CU(cudaHostGetDevicePointer((void **)&s->d_resp, s->h_resp, 0));
+    ABC_CU(cudaHostGetDevicePointer((void **)&s->d_resp_seq, s->h_resp_seq, 0));
+    ABC_CU(cudaHostGetDevicePointer((void **)&s->d_ctl, s->h_ctl, 0));
+    ABC_TRY(ctx->alloc(&s->d_progress, nt, "serve progress"));
+    ABC_TRY(ctx->alloc(&s->d_err, 1, "serve error"));
+    ABC_TRY(ctx->alloc(&s->d_exit_at, 1, "serve exit"));
+    ABC_CU(cudaMemsetAsync(s->d_progress, 0, sizeof(unsigned long long) * nt, ctx->stream));
+    ABC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), ctx->stream));
+    const int64_t tomb_words = (2 * g.m + 31) / 32 + 1;
+    for (int32_t t = 0; t < nt; ++t) {
+        TargetDev T{};
+        T.alpha = ta[t];
+        T.beta = tb[t];
+        ABC_TRY(serve_alloc(ctx, s, &T.M, (size_t)std::max<int64_t>(n, 1), "serve mask"));
+        ABC_TRY(serve_alloc(ctx, s, &T.cnt, (size_t)std::max<int64_t>(n, 1), "serve counts"));
+        ABC_TRY(serve_alloc(ctx, s, &T.deg, (size_t)std::max<int64_t>(n, 1), "serve degrees"));
+        ABC_TRY(serve_alloc(ctx, s, &T.tomb, (size_t)tomb_words, "serve tombstones"));
+        ABC_TRY(serve_alloc(ctx, s, &T.dhead, (size_t)std::max<int64_t>(n, 1), "serve lists"));
+        ABC_TRY(serve_alloc(ctx, s, &T.dpool, (size_t)s->dcap, "serve list pool"));
+        ABC_TRY(serve_alloc(ctx, s, &T.dcount, 1, "serve list pool"));
+        ABC_TRY(serve_alloc(ctx, s, &T.mark, (size_t)std::max<int64_t>(n, 1), "serve marks"));
+        ABC_TRY(serve_alloc(ctx, s, &T.q, (size_t)std::max<int64_t>(2 * n, 1), "serve queue"));
+        ABC_TRY(serve_alloc(ctx, s, &T.epoch, 1, "serve epoch"));
+        T.dcap = (int32_t)s->dcap;
+        ABC_CU(cudaMemsetAsync(T.tomb, 0, sizeof(uint32_t) * tomb_words, ctx->stream));
+        ABC_CU(cudaMemsetAsync(T.dcount, 0, sizeof(int32_t), ctx->stream));
+        ABC_CU(cudaMemsetAsync(T.epoch, 0, sizeof(int32_t), ctx->stream));
+        // the target's core on the current graph, by the single peel
+        ABC_TRY(peel_compute(ctx, ta[t], tb[t], nullptr, nullptr, true));
+        const int32_t pU = (int32_t)cnt_ge(g.cntU_ge, ta[t]), pV = (int32_t)cnt_ge(g.cntV_ge, tb[t]);
+        k_target_init<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, ctx->w.cp, g.nU, g.nV, pU, pV, ta[t], tb[t], T);
+        ctx->stats.launches++;
+        ABC_CU(cudaGetLastError());
+        s->tdev.push_back(T);
+    }
+    ABC_TRY(ctx->alloc(&s->d_targets, nt, "serve targets"));
+    ABC_CU(cudaMemcpyAsync(s->d_targets, s->tdev.data(), sizeof(TargetDev) * nt, cudaMemcpyHostToDevice, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    return ABCORE_OK;
+}
+
+int serve_submit(abcore_ctx *ctx, const abcore_req *reqs, int32_t n, uint64_t *seq_out) {
+    ServeState *s = ctx->serve;
+    if (!s) return ctx->fail(ABCORE_EINVAL, "serve: not started");
+    const Graph &g = ctx->g;
+    for (int32_t i = 0; i < n; ++i) {
+        const abcore_req &r = reqs[i];
+        if (r.u < 0 || r.u >= g.nU || r.v < 0 || r.v >= g.nV) return ctx->fail(ABCORE_EINVAL, "request %d: vertex id out of range", i);
+        if (r.op != ABCORE_INSERT && r.op != ABCORE_DELETE) return ctx->fail(ABCORE_EINVAL, "request %d: bad op", i);
+        if (r.target < 0 || r.target >= (int32_t)s->alphas.size()) return ctx->fail(ABCORE_EINVAL, "request %d: bad target", i);
+    }
+    const unsigned long long low = std::min(min_progress(s), s->consumed);
+    if (s->next_seq + (unsigned long long)n - low > (unsigned long long)s->slots) {
+        ABC_TRY(ensure_loop(ctx, s));
+        return ctx->fail(ABCORE_EBUSY, "serve: request ring full");
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        const unsigned long long k = s->next_seq + i;
+        s->h_req[k % s->slots] = reqs[i];
+        if (seq_out) seq_out[i] = k;
+    }
+    s->next_seq += n;
+    __atomic_store_n(&s->h_ctl[0], s->next_seq, __ATOMIC_SEQ_CST);
+    if (n > 0) s->dirty = true;
+    return ensure_loop(ctx, s);
+}
+
+int serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out) {
+    ServeState *s = ctx->serve;
     *n_out = 0;
-    return ctx->fail(ABCORE_EINVAL, "serve: not available");
+    if (!s) return ctx->fail(ABCORE_EINVAL, "serve: not started");
+    int32_t got = 0;
+    while (got < max && s->consumed < s->next_seq) {
+        const unsigned long long k = s->consumed;
+        const unsigned long long mark = __atomic_load_n(&s->h_resp_seq[k % s->slots], __ATOMIC_ACQUIRE);
+        if (mark != k + 1) break;
+        out[got++] = s->h_resp[k % s->slots];
+        s->consumed++;
+    }
+    *n_out = got;
+    ABC_TRY(check_device_error(ctx, s));
+    return ensure_loop(ctx, s);
 }
-int serve_stop(abcore_ctx *ctx) { return ctx->fail(ABCORE_EINVAL, "serve: not available"); }
-void free_serve(abcore_ctx *ctx) { (void)ctx; }
+
+int serve_stop(abcore_ctx *ctx) {
+    ServeState *s = ctx->serve;
+    if (!s) return ABCORE_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    while (min_progress(s) < s->next_seq) {
+        ABC_TRY(check_device_error(ctx, s));
+        ABC_TRY(ensure_loop(ctx, s));
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(ctx->prm.timeout_ms * 4))
+            return ctx->fail(ABCORE_ETIMEDOUT, "serve: requests did not finish");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    __atomic_store_n(ctl_stop_ptr(s->h_ctl), (int64_t)1, __ATOMIC_SEQ_CST);
+    ABC_CU(cudaStreamSynchronize(s->stream));
+    __atomic_store_n(ctl_stop_ptr(s->h_ctl), (int64_t)0, __ATOMIC_SEQ_CST);
+    s->loop_launched = false;
+    return check_device_error(ctx, s);
+}
+
+int query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta, uint8_t *in_core) {
+    ServeState *s = ctx->serve;
+    int32_t t = -1;
+    if (s)
+        for (size_t i = 0; i < s->alphas.size(); ++i)
+            if (s->alphas[i] == alpha && s->betas[i] == beta) t = (int32_t)i;
+    if (s && s->consumed < s->next_seq)
+        return ctx->fail(ABCORE_EBUSY, "query_edge: poll the outstanding served responses first");
+    if (t < 0) {
+        std::vector<int32_t> a = s ? s->alphas : std::vector<int32_t>(), b = s ? s->betas : std::vector<int32_t>();
+        a.push_back(alpha);
+        b.push_back(beta);
+        ABC_TRY(serve_start(ctx, a.data(), b.data(), (int32_t)a.size(), 1024));
+        s = ctx->serve;
+        t = (int32_t)a.size() - 1;
+    }
+    abcore_req r{op, u, v, t, 0};
+    uint64_t seq = 0;
+    ABC_TRY(serve_submit(ctx, &r, 1, &seq));
+    const auto t0 = std::chrono::steady_clock::now();
+    abcore_resp resp{};
+    for (;;) {
+        int32_t got = 0;
+        ABC_TRY(serve_poll(ctx, &resp, 1, &got));
+        if (got == 1) break;
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(ctx->prm.timeout_ms * 4))
+            return ctx->fail(ABCORE_ETIMEDOUT, "query_edge: no response");
+    }
+    *in_core = resp.in_core;
+    if (resp.status != ABCORE_OK)
+        return ctx->fail(resp.status, resp.status == ABCORE_EEXIST ? "insert: edge already present"
+                                                                   : "delete: edge not present");
+    return ABCORE_OK;
+}
