@@ -159,11 +159,11 @@ def algorithmic_bytes(st):
     b[1] = 4 * st["stream_entries"] + 8 * dec_stream
     # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;
     # per entry 4 B; per decrement 8 B; per push 8 B queue write + 4 B row length;
-    # emission: gather 4 B old2new + 1 B mask per vertex + 4 B count per candidate;
-    # scatter 4 B count per candidate
+    # emission: gather 1 B membership write + 4 B old2new + 1 B membership read + 1 B mask per
+    # vertex, plus 4 B count per candidate; scatter 4 B count per candidate
     dec_casc = st["decrements"] - dec_stream
     b[2] = (28 * st["items"] + 4 * st["entries"] + 8 * dec_casc + 12 * st["pushes"]
-            + 5 * st["emit_gathered"] + 4 * st["candidates"])
+            + 7 * st["emit_gathered"] + 4 * st["candidates"])
     return b
 
 
@@ -350,6 +350,221 @@ def run_peel(args, rank, world, local):
     return line
 
 
+def run_batch(args, rank, world, local):
+    """Batched cores/s: all pairs of the grid in one abcore_compute_batch call (a graph replay)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2606_07148_gb300 import ABCore
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    base = "billion-100Mx50M-1500M" if args.workload == "billion-batch" else args.workload
+    spec, nU, nV, eu, ev = make_inputs(base, dev)
+    m = spec["m"]
+    pairs = [tuple(p) for p in spec["pairs"]]
+    if base.startswith("billion"):
+        pairs = pairs[1:]  # the 8 x 8 grid; the single (64, 64) core is the peel workload
+    core = ABCore(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    core.load_edges(nU, nV, eu, ev)
+    e1.record()
+    torch.cuda.synchronize()
+    csr_ms = e0.elapsed_time(e1)
+    del eu, ev
+    torch.cuda.empty_cache()
+    a = [p[0] for p in pairs]
+    b = [p[1] for p in pairs]
+    mu = torch.empty((len(pairs), nU), dtype=torch.uint8, device=dev)
+    mv = torch.empty((len(pairs), nV), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        core.compute_batch(a, b, mu, mv)
+    core.set_param("timing", 1)
+    core.set_param("reset_stats", 1)
+    st0 = core.stats()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    steps = max(1, args.steps)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record()
+        core.compute_batch(a, b, mu, mv)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    st = core.stats()
+    core.set_param("timing", 0)
+    step_ms = [x.elapsed_time(y) for x, y in evs]
+    ms = allreduce_max(statistics.mean(step_ms), world, dev)
+    value = world * len(pairs) / (ms / 1e3)
+    launches = st["launches"] - st0["launches"]
+    # algorithmic bytes of the batch kernel plus its mask emission
+    by = algorithmic_bytes(st)
+    kb = by[0] + by[1] + by[2]
+    kms = st["kernel_ms"][3]
+    nl = max(st["kernel_launches"][3], 1)
+    achieved = kb / nl / (kms / nl / 1e3) / 1e9 if kms > 0 else 0.0
+    peak, peak_src = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_from_profiles("k_batch", base),
+                "kernel": "k_batch+k_batch_emit", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(kb / nl), "avg_launch_ms": round(kms / nl, 3)}
+    # comparator on the same GPU: one plain abcore_compute launch per pair
+    ou = torch.empty(nU, dtype=torch.uint8, device=dev)
+    ov = torch.empty(nV, dtype=torch.uint8, device=dev)
+    for x, y in pairs[:4]:
+        core.compute(x, y, ou, ov)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(7)
+    c0.record()
+    for x, y in pairs:
+        core.compute(x, y, ou, ov, asynchronous=True)
+    c1.record()
+    core.sync()
+    torch.cuda.synchronize()
+    plain_ms = c0.elapsed_time(c1)
+    mism = 0
+    for i in range(0, len(pairs), max(1, len(pairs) // 8)):
+        core.compute(pairs[i][0], pairs[i][1], ou, ov)
+        mism += int(not (torch.equal(ou, mu[i]) and torch.equal(ov, mv[i])))
+    # end to end with host buffers: every mask of every pair comes back each step
+    hu = torch.empty((len(pairs), nU), dtype=torch.uint8, pin_memory=True)
+    hv = torch.empty((len(pairs), nV), dtype=torch.uint8, pin_memory=True)
+    core.compute_batch(a, b, hu, hv)
+    e2e_steps = max(1, min(steps, 3))
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        core.compute_batch(a, b, hu, hv)
+    e2e_s = allreduce_max((time.perf_counter() - t) / e2e_steps, world, dev)
+    line = {
+        "metric": "batched (alpha,beta)-cores/s", "value": round(value, 2), "unit": "cores/s",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": describe(spec, base), "pairs": len(pairs),
+                   "grid": sorted(set(a)), "csr_build_ms": round(csr_ms, 2),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before every step (256 MB write)", "timed_wall_s": round(t_wall, 3)},
+        "clocks": clk,
+        "e2e": {"value": round(world * len(pairs) / e2e_s, 2), "unit": "cores/s", "h2d_bytes_per_step": 8 * len(pairs),
+                "d2h_bytes_per_step": len(pairs) * (nU + nV)},
+        "gpu_launches": launches, "roofline": roofline,
+        "plain_one_launch_per_pair": {"ms": round(plain_ms, 3), "cores_per_s": round(len(pairs) / (plain_ms / 1e3), 2),
+                                      "batch_speedup": round(plain_ms / ms, 2),
+                                      "spot_check_mismatches": mism},
+        "counters": {k: st[k] for k in ("peels", "entries", "decrements", "stream_entries", "search_probes", "items")},
+    }
+    core.close()
+    return line
+
+
+def run_serve(args, rank, world, local):
+    """Edge-query serving: the update stream replayed open-loop at each arrival rate."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2606_07148_gb300 import ABCore, abi
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spec, nU, nV, eu, ev = make_inputs(args.workload, dev)
+    m = spec["m"]
+    eu_h, ev_h = eu.cpu().numpy(), ev.cpu().numpy()
+    n_ops = args.serve_ops or spec["n_ops"]
+    t0 = time.perf_counter()
+    stream = synth.edge_update_stream(eu_h, ev_h, nU, nV, n_ops, spec["seed"])
+    gen_s = time.perf_counter() - t0
+    targets = [tuple(t) for t in spec["targets"]]
+    reqs = (abi.abcore_req * n_ops)()
+    for k in range(n_ops):
+        reqs[k].op = int(stream.op[k]); reqs[k].u = int(stream.u[k]); reqs[k].v = int(stream.v[k])
+        reqs[k].target = int(stream.target[k]); reqs[k].tag = k
+    req_size = ctypes_sizeof(abi.abcore_req)
+    results = {}
+    answers = {}
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    for rate in spec["rates"]:
+        core = ABCore(local)
+        core.load_edges(nU, nV, eu, ev)
+        core.serve_start(targets, ring_slots=8192)
+        sched = stream.t_unit / rate
+        done_t = np.zeros(n_ops)
+        got = []
+        k = 0
+        start = time.perf_counter()
+        while len(got) < n_ops:
+            now = time.perf_counter() - start
+            if now > sched[-1] + 120.0:
+                raise RuntimeError("serving stalled: %d of %d answered" % (len(got), n_ops))
+            hi = k
+            while hi < n_ops and sched[hi] <= now and hi - k < 4096:
+                hi += 1
+            if hi > k:
+                sub = (abi.abcore_req * (hi - k)).from_buffer(reqs, k * req_size)
+                if core.serve_submit(sub) is not None:
+                    k = hi
+            out = core.serve_poll(8192)
+            if out:
+                tnow = time.perf_counter() - start
+                for r in out:
+                    done_t[r.seq] = tnow
+                got.extend(out)
+        core.serve_stop()
+        lat_ms = (done_t - sched) * 1e3
+        elapsed = done_t.max()
+        results[str(rate)] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 4),
+                              "p99_ms": round(float(np.percentile(lat_ms, 99)), 4),
+                              "achieved_ops_per_s": round(n_ops / elapsed, 1)}
+        answers[rate] = [r.in_core for r in got]
+        core.close()
+    clk = clocks.stop()
+    same = all(answers[r] == answers[spec["rates"][0]] for r in spec["rates"])
+    # comparator on the same GPU: one full plain peel of the graph per query
+    core = ABCore(local)
+    core.load_edges(nU, nV, eu, ev)
+    ou = torch.empty(nU, dtype=torch.uint8, device=dev)
+    ov = torch.empty(nV, dtype=torch.uint8, device=dev)
+    for tg in targets:
+        core.compute(tg[0], tg[1], ou, ov)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    for i in range(40):
+        tg = targets[int(stream.target[i])]
+        core.compute(tg[0], tg[1], ou, ov, asynchronous=True)
+    c1.record()
+    core.sync()
+    torch.cuda.synchronize()
+    plain_qps = 40 / (c0.elapsed_time(c1) / 1e3)
+    core.close()
+    top = results[str(max(spec["rates"]))]
+    line = {
+        "metric": "edge-query p99 latency at the highest arrival rate", "value": top["p99_ms"], "unit": "ms",
+        "n_gpus": world, "steps": len(spec["rates"]), "warmup": 0, "ms_per_step": None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": describe(spec, args.workload), "updates": n_ops,
+                   "targets": [list(t) for t in targets], "stream_gen_s": round(gen_s, 2),
+                   "parallelism": "single"},
+        "rates": results, "answers_identical_across_rates": same,
+        "plain_full_peel_per_query_qps": round(plain_qps, 1), "clocks": clk,
+        "e2e": {"value": top["p99_ms"], "unit": "ms", "h2d_bytes_per_step": n_ops * req_size,
+                "d2h_bytes_per_step": n_ops * ctypes_sizeof(abi.abcore_resp)},
+    }
+    return line
+
+
+def ctypes_sizeof(t):
+    import ctypes
+    return ctypes.sizeof(t)
+
+
 def run_reference(args, rank, world, local):
     """The CPU oracle on the same workload, metric and config (one query per step, rotating)."""
     import numpy as np
@@ -400,6 +615,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="peel-4Mx2M-80M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-ops", type=int, default=0, help="updates per rate (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -413,7 +629,12 @@ def main():
         if rank == 0:
             build()
         barrier(world)
-        line = run_peel(args, rank, world, local)
+        if args.workload.startswith("batch") or args.workload == "billion-batch":
+            line = run_batch(args, rank, world, local)
+        elif args.workload.startswith("serve"):
+            line = run_serve(args, rank, world, local)
+        else:
+            line = run_peel(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -73,6 +73,25 @@ __device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t 
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
 
+// Warp-collective decrement: each lane with `active` lowers the count of candidate y by one.
+// Lanes holding the same y are merged (match.any) into one atomicSub of their number by the
+// lowest of them, so a hub hit by many lanes costs one atomic. The counts fall monotonically, so
+// exactly one merged atomic takes a count from >= thr to < thr: that lane returns true.
+__device__ __forceinline__ bool agg_decrement(int *cnt, int32_t y, bool active, int32_t thr, LaneStats &ls) {
+    const unsigned act = __ballot_sync(ABC_FULL, active);
+    bool crossed = false;
+    if (active) {
+        const unsigned peers = __match_any_sync(act, y);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+            const int c = __popc(peers);
+            const int old = atomicSub(cnt, c);
+            ls.decs++;
+            crossed = old >= thr && old - c < thr;
+        }
+    }
+    return crossed;
+}
+
 // Warp-collective: process the items held by the lanes (`it` == EMPTY: none), spreading the
 // row chunks' entries evenly over the lanes (warp-level load balancing over an exclusive scan).
 __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long it, WarpSmem &sm,
@@ -102,20 +121,18 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
         bool push = false;
         int32_t y = 0;
         int nch = 0;
+        bool hit = false;
+        int32_t thr = 0;
         if (e < L) {
             while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
             const long long pos = sm.start[j] + (e - sm.excl[j]);
             y = __ldg(&a.adj[pos]);
             ls.entries++;
-            int32_t thr;
-            if (cand_of(a, y, sm.upper[j] != 0, thr) && (thr > 0 || !a.skip_zero)) {
-                const int old = atomicSub(&a.cp[y].x, 1);
-                ls.decs++;
-                if (old == thr) {
-                    push = true;
-                    nch = chunks_of(row_len_of(a, y), a.chunk);
-                }
-            }
+            hit = cand_of(a, y, sm.upper[j] != 0, thr) && (thr > 0 || !a.skip_zero);
+        }
+        if (agg_decrement(&a.cp[y].x, y, hit, thr, ls)) {
+            push = true;
+            nch = chunks_of(row_len_of(a, y), a.chunk);
         }
         warp_push(a, push, y, nch, ls);
     }
@@ -260,16 +277,11 @@ __device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool 
                                              LaneStats &ls) {
     bool push = false;
     int nch = 0;
-    if (valid) {
-        int32_t thr;
-        if (cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero)) {
-            const int old = atomicSub(&a.cp[y].x, 1);
-            ls.decs++;
-            if (old == thr) {
-                push = true;
-                nch = chunks_of(row_len_of(a, y), a.chunk);
-            }
-        }
+    int32_t thr = 0;
+    const bool hit = valid && cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero);
+    if (agg_decrement(&a.cp[y].x, y, hit, thr, ls)) {
+        push = true;
+        nch = chunks_of(row_len_of(a, y), a.chunk);
     }
     warp_push(a, push, y, nch, ls);
 }

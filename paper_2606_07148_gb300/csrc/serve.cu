@@ -11,11 +11,19 @@
 // still gives exactly the core of the updated graph G':
 //  * delete (u, v) with both in C: the new core lies inside C, so only a cascade inside C,
 //    started at u and v, is needed; a delete with an endpoint outside C changes nothing;
-//  * insert (u, v): the new core contains C, and every new member lies in a connected piece of
-//    G'[V \ C] that touches u or v (a piece away from e would already have joined C in G).
-//    So a BFS from the non-core endpoints through non-core vertices whose degree meets their
-//    bound finds the only region R that can join; R is peeled with C held fixed and its
-//    survivors join C. If both endpoints are in C, nothing can join.
+//  * insert (u, v): the new core contains C. To find what joins, each target keeps a removal
+//    certificate: a level rho(w) for every vertex w outside C such that fewer than thr(w) of
+//    w's neighbours are in C or have rho >= rho(w) (peeling by increasing rho then removes
+//    every non-core vertex, which proves C is the whole core). Take the new members in order of
+//    rho: each one is an endpoint of e or has a new member with smaller rho as a neighbour,
+//    since otherwise its neighbours in the new core would all lie in C or at rho >= its own,
+//    too few. So every new member is reached from the endpoints along edges of strictly
+//    increasing rho. That region R (non-core vertices meeting their degree bound) is peeled
+//    level by level with C held fixed; its survivors join C, and the levels at which the others
+//    fall, offset past every rho in use, become their new rho. Vertices outside R keep valid
+//    certificates: a neighbour in R had rho at least theirs, and its new rho is larger still.
+//    If both endpoints are in C, nothing can join.
+//  * The delete cascade assigns rho the same way (its levels, offset past every rho in use).
 //
 // Data on the device. The base CSR (internal, degree-ordered ids) is shared and never changes.
 // Each target keeps its own view of the updates -- tombstone bits over base adjacency slots, a
@@ -63,7 +71,12 @@ struct TargetDev {
     int32_t *mark;     // [n] epoch tags for region / cascade membership
     int32_t *q;        // [2n] scratch queue (a region, then the region vertices it peels)
     int32_t *epoch;    // persisted epoch counter
+    int32_t *rho;      // [n] removal certificate level of non-core vertices (RHO_CORE in C)
+    int32_t *base;     // next unused certificate level
+    unsigned long long *st;  // [4] regions grown, region vertices, cascades, vertices cascaded
 };
+
+constexpr int32_t RHO_CORE = 0x7fffffff;
 
 struct ServeArgs {
     const int64_t *off;
@@ -168,24 +181,28 @@ struct BlockQueue {
 __device__ __forceinline__ void bq_push(BlockQueue &Q, int32_t z) { Q.q[atomicAdd(Q.tail, 1)] = z; }
 
 // Cascade inside the core after a delete: members whose in-core count fell below their bound
-// leave, lowering their member neighbours' counts (queued on the exact crossing).
+// leave, lowering their member neighbours' counts (queued on the exact crossing). Vertices
+// leaving at cascade level L get certificate level base + L.
 __device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y) {
     __shared__ int tail;
+    __shared__ int32_t base_s;
     BlockQueue Q{S.q, &tail};
     if (threadIdx.x == 0) {
         tail = 0;
+        base_s = *S.base;
         const int32_t cx = --S.cnt[x], cy = --S.cnt[y];
         if (cx < thr_of(A, S, x)) { S.M[x] = 0; Q.q[tail++] = x; }
         if (cy < thr_of(A, S, y)) { S.M[y] = 0; Q.q[tail++] = y; }
     }
     __syncthreads();
-    int head = 0;
+    int head = 0, level = 0;
     const int warp = threadIdx.x >> 5;
     while (head < tail) {
         const int end = tail;
         __syncthreads();
         for (int i = head + warp; i < end; i += SERVE_WARPS) {
             const int32_t w = S.q[i];
+            if ((threadIdx.x & 31) == 0) S.rho[w] = base_s + level;
             for_neighbours(A, S, w, [&](int32_t z) {
                 if (S.M[z]) {
                     const int old = atomicSub(&S.cnt[z], 1);
@@ -198,39 +215,47 @@ __device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int3
         }
         __syncthreads();
         head = end;
+        ++level;
     }
+    if (threadIdx.x == 0 && tail > 0) {
+        *S.base = base_s + level + 1;
+        S.st[2] += 1;
+        S.st[3] += (unsigned long long)tail;
+    }
+    __syncthreads();
 }
 
-// Region growth and peel after an insert with an endpoint outside the core.
+// Region growth and peel after an insert with an endpoint outside the core (see the header).
 __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y, int32_t ep) {
-    __shared__ int tail, abort_flag;
+    __shared__ int tail;
+    __shared__ int32_t base_s;
     BlockQueue Q{S.q, &tail};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         tail = 0;
-        abort_flag = 0;
+        base_s = *S.base;
         const int32_t ends[2] = {x, y};
         for (int i = 0; i < 2; ++i) {
             const int32_t z = ends[i];
-            if (S.M[z]) continue;
-            if (S.deg[z] < thr_of(A, S, z)) abort_flag = 1;  // z can never join: nothing changes
-            else if (S.mark[z] != ep) {
-                S.mark[z] = ep;
-                Q.q[tail++] = z;
-            }
+            // a non-core endpoint below its bound on degree can neither join nor lose its
+            // certificate (at most deg < thr neighbours can count)
+            if (S.M[z] || S.deg[z] < thr_of(A, S, z) || S.mark[z] == ep) continue;
+            S.mark[z] = ep;
+            Q.q[tail++] = z;
         }
     }
     __syncthreads();
-    if (abort_flag) return;
-    // grow R: non-core vertices meeting their bound on degree, connected to the seeds
+    if (tail == 0) return;
+    // grow R along edges of strictly increasing rho through non-core vertices meeting their bound
     int head = 0;
     while (head < tail) {
         const int end = tail;
         __syncthreads();
         for (int i = head + warp; i < end; i += SERVE_WARPS) {
             const int32_t w = S.q[i];
+            const int32_t rw = S.rho[w];
             for_neighbours(A, S, w, [&](int32_t z) {
-                if (!S.M[z] && S.deg[z] >= thr_of(A, S, z)) {
+                if (!S.M[z] && S.rho[z] > rw && S.deg[z] >= thr_of(A, S, z)) {
                     const int old = atomicExch(&S.mark[z], ep);
                     if (old != ep) bq_push(Q, z);
                 }
@@ -249,7 +274,8 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
         if (lane == 0) S.cnt[w] = c;
     }
     __syncthreads();
-    // peel R with C fixed: removed region vertices get tag ep + 1
+    // peel R level by level with C fixed; region vertices falling at level L get tag ep + 1 and
+    // certificate level base + L
     if (threadIdx.x == 0) tail = R;
     __syncthreads();
     for (int i = threadIdx.x; i < R; i += SERVE_THREADS) {
@@ -261,11 +287,13 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
     }
     __syncthreads();
     head = R;
+    int level = 0;
     while (head < tail) {
         const int end = tail;
         __syncthreads();
         for (int i = head + warp; i < end; i += SERVE_WARPS) {
             const int32_t w = S.q[i];
+            if (lane == 0) S.rho[w] = base_s + level;
             for_neighbours(A, S, w, [&](int32_t z) {
                 if (S.mark[z] == ep) {
                     const int old = atomicSub(&S.cnt[z], 1);
@@ -278,6 +306,7 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
         }
         __syncthreads();
         head = end;
+        ++level;
     }
     // survivors join C; their old-core neighbours gain one in-core neighbour per edge
     for (int i = warp; i < R; i += SERVE_WARPS) {
@@ -290,7 +319,15 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
     __syncthreads();
     for (int i = threadIdx.x; i < R; i += SERVE_THREADS) {
         const int32_t w = S.q[i];
-        if (S.mark[w] == ep) S.M[w] = 1;
+        if (S.mark[w] == ep) {
+            S.M[w] = 1;
+            S.rho[w] = RHO_CORE;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *S.base = base_s + level + 1;
+        S.st[0] += 1;
+        S.st[1] += (unsigned long long)R;
     }
     __syncthreads();
 }
@@ -457,20 +494,46 @@ __global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
     if (threadIdx.x == 0) *S.epoch = ep;
 }
 
-// Target state from a fresh peel: membership, in-core counts, degrees, empty update view.
-__global__ void k_target_init(const int64_t *off, const int2 *cp, int32_t nU, int32_t nV, int32_t pU, int32_t pV,
-                              int32_t alpha, int32_t beta, TargetDev S) {
+// Target state by a level-synchronous peel of the current CSR: membership, in-core counts,
+// degrees, an empty update view, and the removal certificate (rho = the round a vertex falls).
+__global__ void k_lv_init(const int64_t *off, int32_t nU, int32_t nV, TargetDev S, int32_t *front,
+                          unsigned *nfront) {
     const int64_t n = (int64_t)nU + nV;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
-        bool alive;
-        int c = 0;
-        if (x < nU) alive = x < pU && (c = cp[x].x) >= alpha;
-        else alive = x - nU < pV && (c = cp[x].x) >= beta;
-        S.M[x] = alive ? 1 : 0;
-        S.cnt[x] = alive ? c : 0;
-        S.deg[x] = (int32_t)(off[x + 1] - off[x]);
+        const int32_t d = (int32_t)(off[x + 1] - off[x]);
+        const int32_t thr = x < nU ? S.alpha : S.beta;
+        S.cnt[x] = d;
+        S.deg[x] = d;
         S.dhead[x] = -1;
         S.mark[x] = 0;
+        if (d < thr) {
+            S.rho[x] = 0;
+            S.M[x] = 0;
+            front[atomicAdd(nfront, 1u)] = (int32_t)x;
+        } else {
+            S.rho[x] = RHO_CORE;
+            S.M[x] = 1;
+        }
+    }
+}
+
+__global__ void k_lv_round(const int64_t *off, const int32_t *adj, int32_t nU, TargetDev S, const int32_t *fin,
+                           unsigned nin, int32_t *fout, unsigned *nout, int32_t round) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t w = fin[i];
+        for (int64_t p = off[w] + lane; p < off[w + 1]; p += 32) {
+            const int32_t y = adj[p];
+            if (S.rho[y] != RHO_CORE) continue;  // already removed
+            const int32_t thr = y < nU ? S.alpha : S.beta;
+            const int old = atomicSub(&S.cnt[y], 1);
+            if (old == thr) {
+                S.rho[y] = round + 1;
+                S.M[y] = 0;
+                fout[atomicAdd(nout, 1u)] = y;
+            }
+        }
     }
 }
 
@@ -532,7 +595,12 @@ static int64_t *ctl_stop_ptr(unsigned long long *ctl) { return (int64_t *)(ctl +
 
 static bool loop_running(ServeState *s) {
     if (!s->loop_launched) return false;
-    return cudaEventQuery(s->loop_done) == cudaErrorNotReady;
+    const cudaError_t e = cudaEventQuery(s->loop_done);
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();  // "not ready" is a status, not an error: keep it out of later checks
+        return true;
+    }
+    return false;
 }
 
 static unsigned long long min_progress(ServeState *s) {
@@ -566,6 +634,7 @@ static int launch_loop(abcore_ctx *ctx, ServeState *s) {
     A.slots = s->slots;
     A.idle_ns = 200ull * 1000000ull;
     A.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
+    cudaGetLastError();
     ABC_CU(cudaMemsetAsync(s->d_exit_at, 0xff, sizeof(unsigned long long), s->stream));
     k_serve<<<A.ntargets, SERVE_THREADS, 0, s->stream>>>(A);
     ABC_CU(cudaGetLastError());
@@ -719,15 +788,41 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
         ABC_TRY(serve_alloc(ctx, s, &T.mark, (size_t)std::max<int64_t>(n, 1), "serve marks"));
         ABC_TRY(serve_alloc(ctx, s, &T.q, (size_t)std::max<int64_t>(2 * n, 1), "serve queue"));
         ABC_TRY(serve_alloc(ctx, s, &T.epoch, 1, "serve epoch"));
+        ABC_TRY(serve_alloc(ctx, s, &T.rho, (size_t)std::max<int64_t>(n, 1), "serve certificate"));
+        ABC_TRY(serve_alloc(ctx, s, &T.base, 1, "serve certificate"));
+        ABC_TRY(serve_alloc(ctx, s, &T.st, 4, "serve stats"));
+        ABC_CU(cudaMemsetAsync(T.st, 0, 4 * sizeof(unsigned long long), ctx->stream));
         T.dcap = (int32_t)s->dcap;
         ABC_CU(cudaMemsetAsync(T.tomb, 0, sizeof(uint32_t) * tomb_words, ctx->stream));
         ABC_CU(cudaMemsetAsync(T.dcount, 0, sizeof(int32_t), ctx->stream));
         ABC_CU(cudaMemsetAsync(T.epoch, 0, sizeof(int32_t), ctx->stream));
-        // the target's core on the current graph, by the single peel
-        ABC_TRY(peel_compute(ctx, ta[t], tb[t], nullptr, nullptr, true));
-        const int32_t pU = (int32_t)cnt_ge(g.cntU_ge, ta[t]), pV = (int32_t)cnt_ge(g.cntV_ge, tb[t]);
-        k_target_init<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, ctx->w.cp, g.nU, g.nV, pU, pV, ta[t], tb[t], T);
-        ctx->stats.launches++;
+        // the target's core and certificate on the current graph, by a level-synchronous peel
+        {
+            int32_t *fa = T.q, *fb = T.q + std::max<int64_t>(n, 1);  // the scratch queue holds both frontiers
+            unsigned *cnts = nullptr;
+            ABC_TRY(serve_alloc(ctx, s, &cnts, 2, "serve init"));
+            unsigned h[2] = {0, 0};
+            ABC_CU(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned), ctx->stream));
+            k_lv_init<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, g.nU, g.nV, T, fa, cnts);
+            ctx->stats.launches++;
+            ABC_CU(cudaMemcpyAsync(&h[0], cnts, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+            ABC_CU(cudaStreamSynchronize(ctx->stream));
+            int32_t round = 0;
+            while (h[0] > 0) {
+                ABC_CU(cudaMemsetAsync(cnts + 1, 0, sizeof(unsigned), ctx->stream));
+                const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)h[0] * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+                k_lv_round<<<std::max(blocks, 1u), 256, 0, ctx->stream>>>(g.off, g.adj, g.nU, T, fa, h[0], fb, cnts + 1, round);
+                ctx->stats.launches++;
+                ABC_CU(cudaMemcpyAsync(&h[1], cnts + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+                ABC_CU(cudaStreamSynchronize(ctx->stream));
+                std::swap(fa, fb);
+                h[0] = h[1];
+                ++round;
+            }
+            const int32_t base0 = round + 2;
+            ABC_CU(cudaMemcpyAsync(T.base, &base0, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+            ABC_CU(cudaStreamSynchronize(ctx->stream));
+        }
         ABC_CU(cudaGetLastError());
         s->tdev.push_back(T);
     }

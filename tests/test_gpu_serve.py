@@ -37,11 +37,14 @@ def _reqs(stream, lo, hi):
 
 def _serve(core, stream, targets, batch, ring=4096):
     """Submit the stream in chunks of `batch`, polling as we go; responses in sequence order."""
+    import time
     core.serve_start(targets, ring_slots=ring)
     out = []
     k = 0
     n = len(stream)
+    t0 = time.time()
     while k < n or len(out) < n:
+        assert time.time() - t0 < 120, "serving stalled: %d submitted, %d answered" % (k, len(out))
         if k < n:
             hi = min(n, k + batch)
             seq = core.serve_submit(_reqs(stream, k, hi))
