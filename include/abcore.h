@@ -201,6 +201,37 @@ int abcore_graph_info(abcore_ctx *ctx, int32_t *nU, int32_t *nV, int64_t *m,
  * and new2old[nU+nV], the caller's per-layer id of each internal vertex. */
 int abcore_export_csr(abcore_ctx *ctx, int64_t *off, int32_t *adj, int32_t *new2old, uint32_t flags);
 
+/* ---- allocation-free variant (an interface convenience; the paper has no counterpart) ------ */
+
+/* Limits of abcore_compute_static, whose working memory is a fixed array inside the library. */
+#define ABCORE_STATIC_MAX_VERTICES (1 << 20)
+#define ABCORE_STATIC_MAX_ITEMS    ((1 << 20) + (1 << 16))
+
+/* The (alpha, beta)-core without allocating anything: no cudaMalloc, cudaFree or allocating
+ * library routine is called, and no context is needed. It is meant for callers that cannot
+ * allocate device memory at run time -- code running inside another framework that owns the
+ * device's memory pool, plugins that must not grow a host process's device footprint, or
+ * programs that reserve all device memory up front.
+ *   off[nU+nV+1], adj[off[nU+nV]]: the graph in unified ids, on the current device and owned by
+ *     the caller: rows 0..nU-1 are the upper vertices and list lower vertices as nU + v, rows
+ *     nU..nU+nV-1 are the lower vertices and list upper vertices u; every edge appears in both
+ *     rows; rows may be in any order.
+ *   mask_u[nU], mask_v[nV]: device buffers receiving 1 for core members, else 0.
+ *   cuda_stream: the cudaStream_t to run on (NULL = the legacy default stream); the call waits
+ *     for its work on that stream before returning.
+ * Working memory is one file-scope device array of about 13 MiB, held by every GPU that loads
+ * this library until the process exits. Graphs above ABCORE_STATIC_MAX_VERTICES vertices, or
+ * whose rows split into more than ABCORE_STATIC_MAX_ITEMS - nU - nV chunks of 1024 entries
+ * (about 32 million edges at the vertex limit), are rejected with ABCORE_EINVAL. The first call
+ * on each device looks up the array's device address; make that first call before any stream
+ * capture. Every call shares the array and it keeps the last call's contents (each call clears
+ * what must start empty), so calls that overlap on the GPU -- from several host threads or
+ * streams at once -- race and must not be made.
+ * Returns ABCORE_OK, ABCORE_EINVAL, ABCORE_ECUDA or ABCORE_ETIMEDOUT. */
+int abcore_compute_static(int32_t nU, int32_t nV, const int64_t *off, const int32_t *adj,
+                          int32_t alpha, int32_t beta, uint8_t *mask_u, uint8_t *mask_v,
+                          void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

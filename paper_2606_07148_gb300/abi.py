@@ -32,7 +32,11 @@ EXPORTED = [
     "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_query_edge",
     "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
     "abcore_get_stats", "abcore_set_param", "abcore_graph_info", "abcore_export_csr",
+    "abcore_compute_static",
 ]
+
+ABCORE_STATIC_MAX_VERTICES = 1 << 20
+ABCORE_STATIC_MAX_ITEMS = (1 << 20) + (1 << 16)
 
 
 K_INIT, K_STREAM, K_CASCADE, K_BATCH, K_SERVE = 0, 1, 2, 3, 4
@@ -102,6 +106,8 @@ def load_library(path: str = LIB):
         "abcore_set_param": ([_vp, ctypes.c_char_p, ctypes.c_int64], ctypes.c_int),
         "abcore_graph_info": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "abcore_export_csr": ([_vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
+        "abcore_compute_static": ([ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                   _vp, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -135,3 +141,4 @@ abcore_get_stats = _fn("abcore_get_stats")
 abcore_set_param = _fn("abcore_set_param")
 abcore_graph_info = _fn("abcore_graph_info")
 abcore_export_csr = _fn("abcore_export_csr")
+abcore_compute_static = _fn("abcore_compute_static")
