@@ -154,9 +154,10 @@ def algorithmic_bytes(st):
     # init: per candidate 8 B of offsets (consecutive rows share them) + 8 B count/prefix write;
     # 4 B per word probed by the boundary search
     b[0] = 16 * st["init_vertices"] + 4 * st["search_probes"]
-    # stream: 4 B per streamed entry + 8 B per counter decrement (4 B read + 4 B write)
+    # stream (+ the scan after it): 4 B per streamed entry + 8 B per counter decrement (4 B read
+    # + 4 B write) + 4 B per candidate count checked by the scan
     dec_stream = st["stream_decrements"]
-    b[1] = 4 * st["stream_entries"] + 8 * dec_stream
+    b[1] = 4 * st["stream_entries"] + 8 * dec_stream + 4 * st.get("scanned", 0)
     # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;
     # per entry 4 B; per decrement 8 B; per push 8 B queue write + 4 B row length;
     # emission: gather 1 B membership write + 4 B old2new + 1 B membership read + 1 B mask per
@@ -239,6 +240,7 @@ def run_peel(args, rank, world, local):
     m = spec["m"]
     pairs = peel_pairs_for(name, spec)
     core = ABCore(local)
+    apply_params(core, args)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     core.load_edges(nU, nV, eu, ev)
@@ -366,6 +368,7 @@ def run_batch(args, rank, world, local):
     if base.startswith("billion"):
         pairs = pairs[1:]  # the 8 x 8 grid; the single (64, 64) core is the peel workload
     core = ABCore(local)
+    apply_params(core, args)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     core.load_edges(nU, nV, eu, ev)
@@ -451,7 +454,8 @@ def run_batch(args, rank, world, local):
         "config": {"workload": args.workload, "graph": describe(spec, base), "pairs": len(pairs),
                    "grid": sorted(set(a)), "csr_build_ms": round(csr_ms, 2),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed before every step (256 MB write)", "timed_wall_s": round(t_wall, 3)},
+                   "l2": "flushed before every step (256 MB write)", "timed_wall_s": round(t_wall, 3),
+                   "params": args.param},
         "clocks": clk,
         "e2e": {"value": round(world * len(pairs) / e2e_s, 2), "unit": "cores/s", "h2d_bytes_per_step": 8 * len(pairs),
                 "d2h_bytes_per_step": len(pairs) * (nU + nV)},
@@ -560,6 +564,12 @@ def run_serve(args, rank, world, local):
     return line
 
 
+def apply_params(core, args):
+    for kv in args.param:
+        k, v = kv.split("=", 1)
+        core.set_param(k, int(v))
+
+
 def ctypes_sizeof(t):
     import ctypes
     return ctypes.sizeof(t)
@@ -616,6 +626,7 @@ def main():
     ap.add_argument("--workload", default="peel-4Mx2M-80M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-ops", type=int, default=0, help="updates per rate (default: the workload's)")
+    ap.add_argument("--param", action="append", default=[], help="library parameter name=value (repeatable)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

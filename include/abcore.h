@@ -73,6 +73,7 @@ typedef struct {
     int64_t entries;         /* adjacency entries read by the cascade                          */
     int64_t decrements;      /* atomic count decrements, all kernels                           */
     int64_t stream_decrements; /* of which issued while streaming the initial violators' rows  */
+    int64_t scanned;         /* candidates checked for violations after that stream            */
     int64_t pushes;          /* vertices queued for removal                                    */
     int64_t items;           /* cascade work items (row chunks) processed                      */
     int64_t emit_gathered;   /* mask bytes written by a gather over every vertex               */

@@ -47,7 +47,7 @@ class abcore_stats(ctypes.Structure):
     _fields_ = [
         ("peels", ctypes.c_int64), ("candidates", ctypes.c_int64), ("init_vertices", ctypes.c_int64),
         ("search_probes", ctypes.c_int64), ("stream_entries", ctypes.c_int64), ("entries", ctypes.c_int64),
-        ("decrements", ctypes.c_int64), ("stream_decrements", ctypes.c_int64), ("pushes", ctypes.c_int64),
+        ("decrements", ctypes.c_int64), ("stream_decrements", ctypes.c_int64), ("scanned", ctypes.c_int64), ("pushes", ctypes.c_int64),
         ("items", ctypes.c_int64),
         ("emit_gathered", ctypes.c_int64), ("emit_scattered", ctypes.c_int64), ("mask_zeroed", ctypes.c_int64),
         ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64 * K_KINDS),

@@ -313,9 +313,14 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
     } else if (k == "probe_bytes") {
         if (value < 1) return ctx->fail(ABCORE_EINVAL, "probe_bytes must be >= 1");
         p.probe_bytes = (double)value;
-    } else if (k == "batch_groups") {
-        if (value < 0) return ctx->fail(ABCORE_EINVAL, "batch_groups must be >= 0");
-        p.batch_groups = (int)value;
+    } else if (k == "batch_wave") {
+        if (value < 0 || value > 32) return ctx->fail(ABCORE_EINVAL, "batch_wave must be 0..32");
+        p.batch_wave = (int)value;
+        free_batch(ctx);
+    } else if (k == "hub_degree") {
+        if (value < 0) return ctx->fail(ABCORE_EINVAL, "hub_degree must be >= 0");
+        ABC_TRY(abcore_sync(ctx));
+        p.hub_degree = (int)std::min<int64_t>(value, INT32_MAX);
         free_batch(ctx);
     } else if (k == "timing") {
         if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "timing must be 0 or 1");

@@ -40,13 +40,15 @@ struct ChainDev {
     int32_t beta_off;        // betas[beta_off .. beta_off + nsteps): ascending V bounds
     int32_t pU0, pV0;        // step-0 candidate prefixes
     int32_t searchU, searchV;
+    int32_t hubcutU, hubcutV;
     int32_t first_block, nblocks;
     int32_t col;             // column of this chain in lvl
     int64_t sa, ea, sb, eb;  // step-0 violator slices (see stream_range)
 };
 
 struct ChainMem {
-    int2 *cp;
+    int32_t *cnt;
+    int32_t *plen;
     unsigned long long *q;
     PeelCtl *ctl;
     unsigned *bar;           // group barrier: [0] arrivals, [32] generation
@@ -125,7 +127,8 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     PeelArgs a{};
     a.off = B.off;
     a.adj = B.adj;
-    a.cp = mem.cp;
+    a.cnt = mem.cnt;
+    a.plen = mem.plen;
     a.q = mem.q;
     a.qcap = B.qcap;
     a.ctl = mem.ctl;
@@ -138,6 +141,8 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     a.chunk = B.chunk;
     a.searchU = cd.searchU;
     a.searchV = cd.searchV;
+    a.hubcutU = cd.hubcutU;
+    a.hubcutV = cd.hubcutV;
     a.timeout_ns = B.timeout_ns;
     a.skip_zero = 0;  // a V bound of 0 may rise later: keep every count exact
     a.lvl = B.lvl;
@@ -159,6 +164,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
         sdecs = ls.decs - d0;
         ls.decs = d0;
         if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        unsigned long long scanned = 0;
+        abc::scan_range(a, t0, nthreads, ls, scanned);
+        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     }
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
@@ -176,9 +184,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
             int nch = 0;
             if (i < cd.pV0) {
                 x = (int32_t)(B.nU + i);
-                const int2 v = __ldcg(&a.cp[x]);
-                viol = v.x >= prev && v.x < a.thrV;
-                nch = abc::chunks_of(v.y, a.chunk);
+                const int c = __ldcg(&a.cnt[x]);
+                viol = c >= prev && c < a.thrV;
+                if (viol) nch = abc::chunks_of(__ldcg(&a.plen[x]), a.chunk);
             }
             abc::warp_push(a, viol, x, nch, ls);
         }
@@ -305,7 +313,8 @@ void free_batch(abcore_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     destroy_plan(ctx, b);
     for (auto &m : b->mem) {
-        ctx->release(m.cp);
+        ctx->release(m.cnt);
+        ctx->release(m.plen);
         ctx->release(m.q);
         ctx->release(m.ctl);
         ctx->release(m.bar);
@@ -344,7 +353,8 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
     }
     const int C = (int)chains.size();
     const int grid = batch_grid(ctx);
-    const int per_wave = std::max(1, std::min({MAX_CHAINS_PER_WAVE, grid, b->nmem}));
+    int per_wave = std::max(1, std::min({MAX_CHAINS_PER_WAVE, grid, b->nmem}));
+    if (ctx->prm.batch_wave > 0) per_wave = std::min(per_wave, ctx->prm.batch_wave);
     b->betas.clear();
     b->waves.clear();
     for (int w0 = 0; w0 < C; w0 += per_wave) {
@@ -365,6 +375,8 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
             const int mode = pick_mode(ctx, ch.alpha, beta0, d.pU0, d.pV0);
             d.searchU = mode & 1;
             d.searchV = (mode >> 1) & 1;
+            d.hubcutU = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, ctx->prm.hub_degree), d.pU0) : 0;
+            d.hubcutV = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), d.pV0) : 0;
             if (!d.searchU && d.pU0 > 0) {
                 d.sa = g.m + cnt_ge(g.edgesV_ge, beta0);
                 d.ea = 2 * g.m;
@@ -420,7 +432,8 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
                            (long long)MAX_STEPS * 2 * grid * (BATCH_THREADS / 32) * 32 / std::max(want_chains, 1) + 4096;
     if (b->nmem >= want_chains && b->qcap >= qcap) return ABCORE_OK;
     for (auto &m : b->mem) {
-        ctx->release(m.cp);
+        ctx->release(m.cnt);
+        ctx->release(m.plen);
         ctx->release(m.q);
         ctx->release(m.ctl);
         ctx->release(m.bar);
@@ -431,14 +444,15 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     b->nmem = 0;
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
-    const double per_chain = 8.0 * n + 8.0 * qcap + 1.0 * n;
+    const double per_chain = 8.0 * n + 8.0 * qcap + 1.0 * n;  // counts + prefixes, queue, levels
     int fit = (int)std::max(1.0, 0.6 * (double)freeb / per_chain);
     const int chains = std::max(1, std::min(want_chains, fit));
     b->qcap = qcap;
     b->mem.resize(chains);
     for (int c = 0; c < chains; ++c) {
         ChainMem &m = b->mem[c];
-        ABC_TRY(ctx->alloc(&m.cp, (size_t)std::max<int64_t>(n, 1), "batch counts"));
+        ABC_TRY(ctx->alloc(&m.cnt, (size_t)std::max<int64_t>(n, 1), "batch counts"));
+        ABC_TRY(ctx->alloc(&m.plen, (size_t)std::max<int64_t>(n, 1), "batch prefixes"));
         ABC_TRY(ctx->alloc(&m.q, (size_t)qcap, "batch queue"));
         ABC_TRY(ctx->alloc(&m.ctl, 1, "batch control"));
         ABC_TRY(ctx->alloc(&m.bar, 64, "batch barrier"));
@@ -523,7 +537,9 @@ int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32
         destroy_plan(ctx, b);
         std::map<int32_t, int> na;
         for (int32_t i = 0; i < n; ++i) na[alphas[i]]++;
-        ABC_TRY(ensure_memory(ctx, b, std::min<int>((int)na.size(), MAX_CHAINS_PER_WAVE)));
+        int want = std::min<int>((int)na.size(), MAX_CHAINS_PER_WAVE);
+        if (ctx->prm.batch_wave > 0) want = std::min(want, ctx->prm.batch_wave);
+        ABC_TRY(ensure_memory(ctx, b, want));
         ABC_TRY(make_plan(ctx, b, n, alphas, betas));
         b->key_a.assign(alphas, alphas + n);
         b->key_b.assign(betas, betas + n);

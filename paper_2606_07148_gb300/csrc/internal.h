@@ -36,13 +36,15 @@ enum {
     ST_ITEMS = 6,    // cascade work items processed
     ST_STEPS = 7,    // chain steps (batch)
     ST_SDECS = 8,    // atomic decrements issued by the violator stream
+    ST_SCAN = 9,     // candidates checked after the violator stream
 };
 
 // Everything a peel kernel needs, passed by value.
 struct PeelArgs {
     const int64_t *off;      // [n+1] row offsets, internal unified ids
     const int32_t *adj;      // [2m] neighbours, each row ascending
-    int2 *cp;                // [n] {count of live candidate neighbours, row prefix length}
+    int32_t *cnt;            // [n] count of live candidate neighbours (the atomic target)
+    int32_t *plen;           // [n] row prefix a removed candidate walks (candidate neighbours)
     unsigned long long *q;   // [qcap] work queue of (vertex << 32 | chunk); ~0 = empty slot
     long long qcap;
     PeelCtl *ctl;
@@ -53,6 +55,8 @@ struct PeelArgs {
     int32_t grab_div;        // queue items per grab = clamp(available / grab_div, 1, 32)
     int32_t searchU;         // 1: U counts by searching U rows; 0: by streaming V violators
     int32_t searchV;         // 1: V counts by searching V rows; 0: by streaming U violators
+    int32_t hubcutU;         // U ids below this count by search whatever searchU says (and the
+    int32_t hubcutV;         // violator stream skips them); V likewise for ids nU + [0, hubcutV)
     unsigned long long timeout_ns;
     // mask emission
     const int32_t *old2new;  // [n] caller id (layer base + id) -> internal id
@@ -76,10 +80,14 @@ struct Params {
     int mode = -1;             // -1 auto; else bit 0 searchU, bit 1 searchV
     long long timeout_ms = 4000;
     int emit_scatter_max_pct = 5;  // scatter masks when |P| <= this % of n
-    double probe_bytes = 64.0;     // cost model: bytes per search probe
-    int batch_groups = 0;      // 0 = one group per chain
+    double probe_bytes = 32.0;     // cost model: bytes charged per search probe
+    int batch_wave = 4;        // chains sharing the GPU at once (0 = as many as fit, up to 32);
+                               // 4 measured best on a 500M-edge graph (counts stay closer to L2)
     int debug_stall_slots = 0; // test hook: queue slots reserved but never written
     int timing = 0;            // 1: CUDA events around each launch, summed into stats.kernel_ms
+    int hub_degree = 256;      // candidates of at least this degree always count by search: the
+                               // violator stream would hit each of them that many times, and
+                               // atomics on one address serialise (0 = off)
 };
 
 struct Graph {
@@ -108,7 +116,8 @@ struct SlotInfo {
 
 struct PeelWork {
     int64_t n = 0, qcap = 0;
-    int2 *cp = nullptr;
+    int32_t *cnt = nullptr;        // [n]
+    int32_t *plen = nullptr;       // [n]
     unsigned long long *q = nullptr;
     PeelCtl *ctl = nullptr;        // [CTL_RING] device control blocks
     PeelCtl *ctl_host = nullptr;   // [CTL_RING] pinned readback

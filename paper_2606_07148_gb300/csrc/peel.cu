@@ -61,9 +61,21 @@ __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t s
     }
 }
 
+__global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
+    LaneStats ls;
+    unsigned long long scanned = 0;
+    abc::scan_range(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls, scanned);
+    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)scanned);
+    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
+    if ((threadIdx.x & 31) == 0) {
+        if (v0) atomicAdd(&a.ctl->st[ST_SCAN], v0);
+        if (v1) atomicAdd(&a.ctl->st[ST_PUSHES], v1);
+    }
+}
+
 __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
-    if (x < a.nU) return x < a.pU && __ldcg(&a.cp[x].x) >= a.thrU;
-    return x < a.nU + a.pV && __ldcg(&a.cp[x].x) >= a.thrV;
+    if (x < a.nU) return x < a.pU && __ldcg(&a.cnt[x]) >= a.thrU;
+    return x < a.nU + a.pV && __ldcg(&a.cnt[x]) >= a.thrV;
 }
 
 __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
@@ -129,9 +141,10 @@ int peel_prepare(abcore_ctx *ctx) {
     // every vertex is queued at most once, as ceil(row / chunk) items; idle warps may also hold
     // one ticket batch each beyond the last item
     const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 + (int64_t)ctx->num_sms * 64 * 32;
-    if (w.n == n && w.qcap >= qcap && w.cp) return ABCORE_OK;
+    if (w.n == n && w.qcap >= qcap && w.cnt) return ABCORE_OK;
     free_peel(ctx);
-    ABC_TRY(ctx->alloc(&w.cp, (size_t)std::max<int64_t>(n, 1), "peel counts"));
+    ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(n, 1), "peel counts"));
+    ABC_TRY(ctx->alloc(&w.plen, (size_t)std::max<int64_t>(n, 1), "peel prefixes"));
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
@@ -149,7 +162,8 @@ int peel_prepare(abcore_ctx *ctx) {
 
 void free_peel(abcore_ctx *ctx) {
     PeelWork &w = ctx->w;
-    ctx->release(w.cp);
+    ctx->release(w.cnt);
+    ctx->release(w.plen);
     ctx->release(w.q);
     ctx->release(w.ctl);
     ctx->release(w.stage);
@@ -169,23 +183,32 @@ void free_peel(abcore_ctx *ctx) {
 }
 
 // Cost model: per layer, count by searching the candidates' rows, or by streaming the rows of
-// the other layer's initial violators? Both reach the same counts; pick the cheaper in bytes.
+// the other layer's initial violators? Both reach the same counts. Costs are in units of one
+// random 32-byte sector read (a search probe), calibrated by measurement on this GPU: a streamed
+// adjacency entry ~0.08, a stream decrement (atomic without return, L2-resident) ~0.8, a
+// candidate's count init ~0.5. Hubs (degree >= hub_degree) count by search in both cases.
 int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, int32_t pV) {
     const Graph &g = ctx->g;
     if (ctx->prm.mode >= 0) return ctx->prm.mode & 3;
     const double m = (double)std::max<int64_t>(g.m, 1);
-    const double eU = (double)cnt_ge(g.edgesU_ge, alpha);  // sum of degrees of U candidates
-    const double eV = (double)cnt_ge(g.edgesV_ge, beta);
-    const double fU = eU / m, fV = eV / m;
-    auto search_cost = [&](int64_t p, double edges) {
-        if (p == 0) return 0.0;
-        const double avg = edges / (double)p;
-        return (double)p * (16.0 + ctx->prm.probe_bytes * (1.0 + std::log2(std::max(avg, 2.0))));
+    const double pb = ctx->prm.probe_bytes / 32.0;  // relative probe cost (default 1)
+    const int hd = ctx->prm.hub_degree > 0 ? ctx->prm.hub_degree : INT32_MAX;
+    auto layer = [&](int64_t p, int32_t thr, const std::vector<int64_t> &cnt, const std::vector<int64_t> &edges,
+                     double other_violator_entries) {
+        // non-hub candidates: degree in [thr, hd)
+        const int32_t top = std::max(thr, hd);
+        const double pn = (double)(p - std::min<int64_t>(p, cnt_ge(cnt, top)));
+        const double en = (double)(cnt_ge(edges, thr) - cnt_ge(edges, top));
+        const double avg = pn > 0 ? en / pn : 1.0;
+        const double search = pn * (0.5 + pb * (1.0 + std::log2(std::max(avg, 1.0))));
+        // stream: every violator entry is read; the share landing on non-hub candidates decrements
+        const double stream = pn * 0.7 + other_violator_entries * (0.08 + 0.8 * (en / m));
+        return search <= stream;
     };
-    // U counts: search U rows, or stream the rows of V violators (m - eV entries)
-    const double sU = search_cost(pU, eU), tU = (m - eV) * (4.0 + 8.0 * fU) + 12.0 * pU;
-    const double sV = search_cost(pV, eV), tV = (m - eU) * (4.0 + 8.0 * fV) + 12.0 * pV;
-    return (sU <= tU ? 1 : 0) | (sV <= tV ? 2 : 0);
+    const double eU = (double)cnt_ge(g.edgesU_ge, alpha), eV = (double)cnt_ge(g.edgesV_ge, beta);
+    const bool sU = layer(pU, alpha, g.cntU_ge, g.edgesU_ge, m - eV);
+    const bool sV = layer(pV, beta, g.cntV_ge, g.edgesV_ge, m - eU);
+    return (sU ? 1 : 0) | (sV ? 2 : 0);
 }
 
 int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
@@ -208,7 +231,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     PeelArgs a{};
     a.off = g.off;
     a.adj = g.adj;
-    a.cp = w.cp;
+    a.cnt = w.cnt;
+    a.plen = w.plen;
     a.q = w.q;
     a.qcap = w.qcap;
     a.ctl = ctl;
@@ -223,6 +247,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
     a.searchU = mode & 1;
     a.searchV = (mode >> 1) & 1;
+    a.hubcutU = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, ctx->prm.hub_degree), pU) : 0;
+    a.hubcutV = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), pV) : 0;
     a.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
     a.old2new = g.old2new;
     a.new2old = g.new2old;
@@ -277,6 +303,11 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             k_stream<<<(unsigned)std::max<int64_t>(gs, 1), STREAM_THREADS, 0, ctx->stream>>>(a, sa, ea, sb, eb);
             si.has_stream = true;
             ctx->stats.launches++;
+            // the candidates counted by degree that the stream pushed below their bound
+            const int64_t ns = (a.searchU ? 0 : (int64_t)pU - a.hubcutU) + (a.searchV ? 0 : (int64_t)pV - a.hubcutV);
+            const int64_t gsc = std::min<int64_t>((ns + 255) / 256, (int64_t)ctx->num_sms * 16);
+            k_scan<<<(unsigned)std::max<int64_t>(gsc, 1), 256, 0, ctx->stream>>>(a);
+            ctx->stats.launches++;
         }
     }
     if (ctx->prm.debug_stall_slots > 0) k_stall<<<1, 1, 0, ctx->stream>>>(ctl, w.qcap, ctx->prm.debug_stall_slots);
@@ -323,6 +354,7 @@ int peel_finish(abcore_ctx *ctx) {
         s.entries += (int64_t)c.st[ST_ENTRIES];
         s.decrements += (int64_t)c.st[ST_DECS] + (int64_t)c.st[ST_SDECS];
         s.stream_decrements += (int64_t)c.st[ST_SDECS];
+        s.scanned += (int64_t)c.st[ST_SCAN];
         s.pushes += (int64_t)c.st[ST_PUSHES];
         s.items += (int64_t)c.st[ST_ITEMS];
         if (si.emit == 1) s.emit_gathered += si.n;

@@ -32,6 +32,17 @@ struct LaneStats {
     unsigned long long entries = 0, decs = 0, pushes = 0, items = 0;
 };
 
+// Adjacency is read once per peel: load it with the evict-first (streaming) policy so it does
+// not push the counts -- the atomics' working set -- out of L2.
+__device__ __forceinline__ int32_t ld_adj(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ int4 ld_adj4(const int4 *p) { return __ldcs(p); }
+
+// A violator-stream entry y skips a hub: its count came from a search and already excludes
+// every initial violator.
+__device__ __forceinline__ bool stream_skips(const PeelArgs &a, int32_t y, bool upper_row) {
+    return upper_row ? (y - a.nU < a.hubcutV) : (y < a.hubcutU);
+}
+
 // Candidate test and bound of a neighbour y seen from a row of layer `upper_row`.
 __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper_row, int32_t &thr) {
     if (upper_row) {
@@ -44,7 +55,7 @@ __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper
 
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in
 // cp[x].y (the full degree when its layer's counts came from the full rows).
-__device__ __forceinline__ int row_len_of(const PeelArgs &a, int32_t y) { return __ldcg(&a.cp[y].y); }
+__device__ __forceinline__ int row_len_of(const PeelArgs &a, int32_t y) { return __ldcg(&a.plen[y]); }
 
 // Warp-collective: lanes with `want` queue vertex y as nch items (nch may be 0).
 __device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t y, int nch, LaneStats &ls) {
@@ -73,24 +84,9 @@ __device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t 
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
 
-// Warp-collective decrement: each lane with `active` lowers the count of candidate y by one.
-// Lanes holding the same y are merged (match.any) into one atomicSub of their number by the
-// lowest of them, so a hub hit by many lanes costs one atomic. The counts fall monotonically, so
-// exactly one merged atomic takes a count from >= thr to < thr: that lane returns true.
-__device__ __forceinline__ bool agg_decrement(int *cnt, int32_t y, bool active, int32_t thr, LaneStats &ls) {
-    const unsigned act = __ballot_sync(ABC_FULL, active);
-    bool crossed = false;
-    if (active) {
-        const unsigned peers = __match_any_sync(act, y);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
-            const int c = __popc(peers);
-            const int old = atomicSub(cnt, c);
-            ls.decs++;
-            crossed = old >= thr && old - c < thr;
-        }
-    }
-    return crossed;
-}
+// Entries handled per lane per step by the streaming and cascade loops: the loads, then the
+// atomics, of one step are independent, so they overlap instead of waiting one at a time.
+constexpr int ILP = 4;
 
 // Warp-collective: process the items held by the lanes (`it` == EMPTY: none), spreading the
 // row chunks' entries evenly over the lanes (warp-level load balancing over an exclusive scan).
@@ -116,25 +112,40 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
     sm.upper[lane] = upper;
     __syncwarp();
     int j = 0;
-    for (int b = 0; b < L; b += 32) {
-        const int e = b + lane;
-        bool push = false;
-        int32_t y = 0;
-        int nch = 0;
-        bool hit = false;
-        int32_t thr = 0;
-        if (e < L) {
-            while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
-            const long long pos = sm.start[j] + (e - sm.excl[j]);
-            y = __ldg(&a.adj[pos]);
-            ls.entries++;
-            hit = cand_of(a, y, sm.upper[j] != 0, thr) && (thr > 0 || !a.skip_zero);
+    for (int b = 0; b < L; b += 32 * ILP) {
+        int32_t y[ILP];
+        int32_t thr[ILP];
+        bool hit[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const int e = b + 32 * u + lane;
+            hit[u] = false;
+            y[u] = 0;
+            thr[u] = 0;
+            if (e < L) {
+                while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
+                y[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
+                thr[u] = sm.upper[j];  // layer of the row, resolved below
+                hit[u] = true;
+            }
         }
-        if (agg_decrement(&a.cp[y].x, y, hit, thr, ls)) {
-            push = true;
-            nch = chunks_of(row_len_of(a, y), a.chunk);
+        int old[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (hit[u]) {
+                ls.entries++;
+                int32_t t;
+                hit[u] = cand_of(a, y[u], thr[u] != 0, t) && (t > 0 || !a.skip_zero);
+                thr[u] = t;
+            }
+            old[u] = hit[u] ? atomicSub(&a.cnt[y[u]], 1) : 0;
         }
-        warp_push(a, push, y, nch, ls);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (hit[u]) ls.decs++;
+            const bool push = hit[u] && old[u] == thr[u];
+            warp_push(a, push, y[u], push ? chunks_of(row_len_of(a, y[u]), a.chunk) : 0, ls);
+        }
     }
     __syncwarp();
 }
@@ -241,7 +252,8 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_
             const bool upper = x < a.nU;
             const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
             int len;
-            if (upper ? a.searchU : a.searchV) {
+            const bool hubx = upper ? x < a.hubcutU : x - a.nU < a.hubcutV;
+            if ((upper ? a.searchU : a.searchV) || hubx) {
                 const int32_t bound = upper ? a.nU + a.pV : a.pU;
                 if (e == s) {
                     len = 0;
@@ -262,7 +274,8 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_
             } else {
                 len = (int)(e - s);
             }
-            a.cp[x] = make_int2(len, len);
+            a.cnt[x] = len;
+            a.plen[x] = len;
             inits++;
             const int32_t thr = upper ? a.thrU : a.thrV;
             viol = len < thr;
@@ -272,18 +285,16 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_
     }
 }
 
-// One adjacency entry y of an initial violator's row: decrement y if it is a candidate.
+// One adjacency entry y of an initial violator's row: lower y's count if y is a candidate that
+// counts by degree. No value is returned: whether a count fell below its bound is decided by
+// scan_range once the whole stream is done (atomics without a return run faster).
 __device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool from_upper, bool valid,
                                              LaneStats &ls) {
-    bool push = false;
-    int nch = 0;
     int32_t thr = 0;
-    const bool hit = valid && cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero);
-    if (agg_decrement(&a.cp[y].x, y, hit, thr, ls)) {
-        push = true;
-        nch = chunks_of(row_len_of(a, y), a.chunk);
+    if (valid && cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero) && !stream_skips(a, y, from_upper)) {
+        atomicAdd(&a.cnt[y], -1);
+        ls.decs++;
     }
-    warp_push(a, push, y, nch, ls);
 }
 
 // Stream the rows of the initial violators (the first peel round): slice A = adj[sa, ea) holds
@@ -306,26 +317,55 @@ __device__ __forceinline__ void stream_range(const PeelArgs &a, int64_t sa, int6
             int32_t y = 0;
             if (valid) {
                 const int64_t pos = i < (a0 - s) ? s + i : a1 + (i - (a0 - s));
-                y = __ldg(&a.adj[pos]);
+                y = ld_adj(&a.adj[pos]);
                 ents++;
             }
             stream_entry(a, y, from_upper, valid, ls);
         }
         const int64_t nv = (a1 - a0) >> 2;
         const int4 *v4 = reinterpret_cast<const int4 *>(a.adj + a0);
-        for (int64_t b = t0 - lane; b < nv; b += nthreads) {
-            const int64_t i = b + lane;
-            const bool valid = i < nv;
-            int4 q = make_int4(0, 0, 0, 0);
-            if (valid) {
-                q = __ldg(&v4[i]);
-                ents += 4;
-            }
-            stream_entry(a, q.x, from_upper, valid, ls);
-            stream_entry(a, q.y, from_upper, valid, ls);
-            stream_entry(a, q.z, from_upper, valid, ls);
-            stream_entry(a, q.w, from_upper, valid, ls);
+        // two 16-byte loads per lane per step
+        for (int64_t b = 2 * (t0 - lane); b < nv; b += 2 * nthreads) {
+            const int64_t i0 = b + lane, i1 = b + 32 + lane;
+            const bool v0 = i0 < nv, v1 = i1 < nv;
+            int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+            if (v0) q0 = ld_adj4(&v4[i0]);
+            if (v1) q1 = ld_adj4(&v4[i1]);
+            ents += (v0 ? 4 : 0) + (v1 ? 4 : 0);
+            stream_entry(a, q0.x, from_upper, v0, ls);
+            stream_entry(a, q0.y, from_upper, v0, ls);
+            stream_entry(a, q0.z, from_upper, v0, ls);
+            stream_entry(a, q0.w, from_upper, v0, ls);
+            stream_entry(a, q1.x, from_upper, v1, ls);
+            stream_entry(a, q1.y, from_upper, v1, ls);
+            stream_entry(a, q1.z, from_upper, v1, ls);
+            stream_entry(a, q1.w, from_upper, v1, ls);
         }
+    }
+}
+
+// After the violator stream: queue the candidates counted by degree whose count fell below
+// their bound (hubs and searched layers were queued by init_range). Warp-collective; `t0` is
+// this thread's index among nthreads.
+__device__ __forceinline__ void scan_range(const PeelArgs &a, int64_t t0, int64_t nthreads, LaneStats &ls,
+                                           unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    const int64_t u0 = a.searchU ? a.pU : a.hubcutU;  // U ids [u0, pU) counted by degree
+    const int64_t v0 = a.searchV ? a.pV : a.hubcutV;  // V ids nU + [v0, pV)
+    const int64_t nu = a.pU - u0, total = nu + (a.pV - v0);
+    for (int64_t b = t0 - lane; b < total; b += nthreads) {
+        const int64_t i = b + lane;
+        bool viol = false;
+        int32_t x = 0;
+        int nch = 0;
+        if (i < total) {
+            x = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
+            const int c = __ldcg(&a.cnt[x]);
+            viol = c < (x < a.nU ? a.thrU : a.thrV);
+            if (viol) nch = chunks_of(__ldcg(&a.plen[x]), a.chunk);
+            scanned++;
+        }
+        warp_push(a, viol, x, nch, ls);
     }
 }
 
