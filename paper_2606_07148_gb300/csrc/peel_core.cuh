@@ -150,7 +150,8 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
     __syncwarp();
 }
 
-// Warp-collective cascade loop: returns 1 when the queue drained, 0 on error.
+// Block-collective cascade loop (every warp of the block calls it): returns 1 when the queue
+// drained, 0 on error.
 //
 // Work is handed out by ticket: lane 0 takes k consecutive slot numbers with one atomicAdd on
 // `head` (k grows with the visible backlog), and lane l owns slot base + l. Pushers fill slots
@@ -160,14 +161,27 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
 // nothing is in flight, so nothing can be queued any more: every ticket at or above tail will
 // never be filled and its holder leaves. (done is read before tail; both only grow and
 // done <= tail, so equality at those two reads proves the queue drained.)
+//
+// An idle warp reads done and tail only on every 16th idle poll (the block's first warp on every
+// one) and publishes a verdict in shared memory for the rest of its block; otherwise it polls
+// only its own slots. (Thousands of idle warps polling the two shared words on every iteration
+// would saturate the L2 slice that also serves the pushers' atomics.)
 __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, LaneStats &ls, int grab_div) {
+    __shared__ volatile int s_verdict;  // 0 running, 1 drained, 3 error
     const int lane = threadIdx.x & 31;
+    const bool leader = (threadIdx.x >> 5) == 0;
+    if (threadIdx.x == 0) s_verdict = 0;
+    __syncthreads();
     unsigned long long idle_since = now_ns(), last_done = ~0ull;
     int st = 2;  // this lane's ticket: 0 waiting, 2 none
     unsigned long long my = 0;
     unsigned sleep_ns = 32;
+    unsigned idle_polls = 0;
     for (;;) {
         if (__ballot_sync(ABC_FULL, st == 0) == 0) {  // no ticket held: take new ones
+            // lane 0 reads the block's verdict for the whole warp, so the warp stays converged
+            const int sv = __shfl_sync(ABC_FULL, lane == 0 ? s_verdict : 0, 0);
+            if (sv != 0) return sv == 1 ? 1 : 0;
             unsigned long long base = 0;
             int k = 1;
             if (lane == 0) {
@@ -200,37 +214,36 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
             if (lane == 0) atomicAdd(&a.ctl->done, (unsigned long long)__popc(have));
             idle_since = now_ns();
             sleep_ns = 32;
-            if (ld_relaxed_i32(&a.ctl->err) != 0) return 0;
             continue;
         }
-        // nothing arrived: is the queue drained, is there an error, or has it stalled?
-        int verdict = 0;  // 0 keep waiting, 1 drained, 3 error
-        unsigned long long tcur = 0;
-        if (lane == 0) {
-            const unsigned long long d = ld_acquire(&a.ctl->done);
-            tcur = ld_acquire(&a.ctl->tail);
-            if (d == tcur) verdict = 1;
-            else if (ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
-            else if (d != last_done) {  // the device is making progress: restart the clock
-                last_done = d;
-                idle_since = now_ns();
-            } else if (now_ns() - idle_since > a.timeout_ns) {
-                set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
-                verdict = 3;
+        // nothing arrived: drained, error, or keep waiting
+        int verdict = __shfl_sync(ABC_FULL, lane == 0 ? s_verdict : 0, 0);
+        if (verdict == 0 && (leader || (++idle_polls & 15) == 0)) {
+            if (lane == 0) {
+                const unsigned long long d = ld_acquire(&a.ctl->done);
+                const unsigned long long tcur = ld_acquire(&a.ctl->tail);
+                if (d == tcur) verdict = 1;
+                else if (ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
+                else if (d != last_done) {  // the device is making progress: restart the clock
+                    last_done = d;
+                    idle_since = now_ns();
+                } else if (now_ns() - idle_since > a.timeout_ns) {
+                    set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
+                    verdict = 3;
+                }
+                if (verdict != 0) s_verdict = verdict;
             }
+            verdict = __shfl_sync(ABC_FULL, verdict, 0);
         }
-        verdict = __shfl_sync(ABC_FULL, verdict, 0);
         if (verdict == 3) return 0;
         if (verdict == 1) {
-            tcur = __shfl_sync(ABC_FULL, tcur, 0);
-            // a ticket below tail must be filled already (everything reserved was processed,
-            // and only its holder processes it), so every waiting ticket here is >= tail
-            if (st == 0 && my >= tcur) st = 2;
-            if (__ballot_sync(ABC_FULL, st == 0) == 0) return 1;
-            continue;
+            // drained: nothing can be queued any more, so every ticket still waiting is at or
+            // above tail and will never be filled (a ticket below tail would be filled and,
+            // being only its holder's to process, would keep done below tail)
+            return 1;
         }
         __nanosleep(sleep_ns);
-        if (sleep_ns < 1024) sleep_ns <<= 1;
+        if (sleep_ns < 256) sleep_ns <<= 1;
     }
 }
 
