@@ -65,6 +65,7 @@ struct BatchArgs {
     uint8_t *lvl;
     int32_t lvl_stride;
     int32_t chunk;
+    uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
 };
@@ -83,14 +84,11 @@ __device__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl, bool fixup, un
         if (arrived == (unsigned)G - 1) {
             atomicExch(bar, 0u);
             if (fixup) {
-                // tickets handed out but never filled lie in [tail, head): skip them so the next
-                // step's pushes land in slots nobody holds
-                const unsigned long long h = abc::ld_relaxed(&ctl->head);
+                // the cascade closed the queue: the tickets it voided, [tail, old head), were
+                // emptied by their holders, so the next step's tickets restart at tail
                 const unsigned long long t = abc::ld_relaxed(&ctl->tail);
-                const unsigned long long mx = h > t ? h : t;
-                atomicExch(&ctl->head, mx);
-                atomicExch(&ctl->tail, mx);
-                atomicExch(&ctl->done, mx);
+                atomicExch(&ctl->head, t);
+                atomicExch(&ctl->done, t);
             }
             __threadfence();
             atomicAdd(bar + 32, 1u);
@@ -149,6 +147,10 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     a.lvl_stride = B.lvl_stride;
     a.lvl_col = cd.col;
     a.step = 0;
+    a.flags = B.flags;
+    a.flag_first = cd.first_block;
+    a.flag_count = G;
+    a.epoch = 1;
     const int grab_div = max(1, G * (BATCH_THREADS / 32) / 8);
 
     const int64_t t0 = (int64_t)r * blockDim.x + threadIdx.x;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     LaneStats ls;
     unsigned long long probes = 0, inits = 0, ents = 0, sdecs = 0;
 
-    abc::init_range(a, t0, nthreads, ls, probes, inits);
+    abc::init_range(a, smem[wib].push, t0, nthreads, ls, probes, inits);
     if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     if (cd.ea > cd.sa || cd.eb > cd.sb) {
         const unsigned long long d0 = ls.decs;
@@ -165,18 +167,20 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
         ls.decs = d0;
         if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         unsigned long long scanned = 0;
-        abc::scan_range(a, t0, nthreads, ls, scanned);
+        abc::scan_range(a, smem[wib].push, t0, nthreads, ls, scanned);
         if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     }
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
-    (void)abc::cascade_loop(a, smem[wib], ls, grab_div);
+    (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
     if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     for (int j = 1; j < cd.nsteps; ++j) {
         const int32_t prev = a.thrV;
         a.thrV = B.betas[cd.beta_off + j];
         a.step = j;
+        a.epoch = (uint32_t)j + 1;
         // V vertices alive after step j-1 (count >= previous bound) that miss the new bound
+        int pc = 0;
         for (int64_t b = t0 - (threadIdx.x & 31); b < cd.pV0; b += nthreads) {
             const int64_t i = b + (threadIdx.x & 31);
             bool viol = false;
@@ -186,12 +190,13 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
                 x = (int32_t)(B.nU + i);
                 const int c = __ldcg(&a.cnt[x]);
                 viol = c >= prev && c < a.thrV;
-                if (viol) nch = abc::chunks_of(__ldcg(&a.plen[x]), a.chunk);
+                if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
             }
-            abc::warp_push(a, viol, x, nch, ls);
+            abc::push_add(a, smem[wib].push, pc, viol, x, nch, ls);
         }
+        abc::push_flush(a, smem[wib].push, pc);
         if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
-        (void)abc::cascade_loop(a, smem[wib], ls, grab_div);
+        (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     }
 out:
@@ -279,6 +284,7 @@ struct BatchState {
     ChainMem *d_mem = nullptr;
     uint8_t *lvl = nullptr;
     int lvl_stride = 0;
+    uint32_t *flags = nullptr;          // [grid * 32] per-block queue-closed flags (epochs)
     PeelCtl *ctl_host = nullptr;        // pinned: [waves x MAX_CHAINS_PER_WAVE]
     long long qcap = 0;
     bool q_dirty = false;
@@ -321,6 +327,7 @@ void free_batch(abcore_ctx *ctx) {
     }
     ctx->release(b->d_mem);
     ctx->release(b->lvl);
+    ctx->release(b->flags);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -463,6 +470,7 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     ABC_CU(cudaMemcpy(b->d_mem, b->mem.data(), sizeof(ChainMem) * chains, cudaMemcpyHostToDevice));
     b->lvl_stride = ((std::min(chains, MAX_CHAINS_PER_WAVE) + 3) / 4) * 4;
     ABC_TRY(ctx->alloc(&b->lvl, (size_t)std::max<int64_t>(n, 1) * b->lvl_stride, "batch levels"));
+    if (!b->flags) ABC_TRY(ctx->alloc(&b->flags, (size_t)grid * 32, "batch close flags"));
     b->nmem = chains;
     ABC_CU(cudaStreamSynchronize(ctx->stream));
     return ABCORE_OK;
@@ -480,6 +488,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
             ABC_CU(cudaMemsetAsync(b->mem[c].bar, 0, 64 * sizeof(unsigned), ctx->stream));
         }
         ABC_CU(cudaMemsetAsync(b->lvl, 0xff, (size_t)n * b->lvl_stride, ctx->stream));
+        ABC_CU(cudaMemsetAsync(b->flags, 0, sizeof(uint32_t) * (size_t)w.grid * 32, ctx->stream));
         BatchArgs B{};
         B.off = g.off;
         B.adj = g.adj;
@@ -492,6 +501,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.lvl = b->lvl;
         B.lvl_stride = b->lvl_stride;
         B.chunk = std::max(ctx->prm.chunk, 32);
+        B.flags = b->flags;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
         void *args[] = {&B};

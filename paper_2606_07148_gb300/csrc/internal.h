@@ -69,7 +69,11 @@ struct PeelArgs {
     // lvl[vertex * lvl_stride + lvl_col] (lvl == nullptr: no record)
     uint8_t *lvl;
     int32_t lvl_stride, lvl_col, step;
-    int32_t pad2;
+    // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
+    // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
+    uint32_t *flags;
+    int32_t flag_first, flag_count;
+    uint32_t epoch;
 };
 
 struct Params {
@@ -129,6 +133,9 @@ struct PeelWork {
     uint8_t *stage = nullptr;      // [n] staging for host-pointer masks
     uint8_t *alive = nullptr;      // [n] membership in internal order
     bool q_dirty = false;          // queue not known to be all-empty
+    uint32_t *flags = nullptr;     // [grid * 32] per-block queue-closed flags (epochs)
+    int flag_blocks = 0;
+    uint32_t epoch = 0;            // last cascade epoch handed out
 };
 
 struct BatchState;

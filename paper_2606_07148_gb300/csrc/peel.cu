@@ -31,9 +31,10 @@ constexpr int INIT_THREADS = 256;
 constexpr int STREAM_THREADS = 256;
 
 __global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
+    __shared__ abc::PushBuf<64> pbuf[INIT_THREADS / 32];
     LaneStats ls;
     unsigned long long probes = 0, inits = 0;
-    abc::init_range(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls,
+    abc::init_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls,
                     probes, inits);
     unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)inits);
     unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)probes);
@@ -62,9 +63,10 @@ __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t s
 }
 
 __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
+    __shared__ abc::PushBuf<64> pbuf[256 / 32];
     LaneStats ls;
     unsigned long long scanned = 0;
-    abc::scan_range(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls, scanned);
+    abc::scan_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls, scanned);
     unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)scanned);
     unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
     if ((threadIdx.x & 31) == 0) {
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     LaneStats ls;
-    const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div);
+    const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div, blockIdx.x == 0 && wib == 0);
     abc::flush_stats(a, ls);
     if (!ok || a.emit == 0) return;
     const int64_t n = (int64_t)a.nU + a.nV;
@@ -141,7 +143,7 @@ int peel_prepare(abcore_ctx *ctx) {
     // every vertex is queued at most once, as ceil(row / chunk) items; idle warps may also hold
     // one ticket batch each beyond the last item
     const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 + (int64_t)ctx->num_sms * 64 * 32;
-    if (w.n == n && w.qcap >= qcap && w.cnt) return ABCORE_OK;
+    if (w.n == n && w.qcap >= qcap && w.cnt && w.flag_blocks >= cascade_grid(ctx)) return ABCORE_OK;
     free_peel(ctx);
     ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(n, 1), "peel counts"));
     ABC_TRY(ctx->alloc(&w.plen, (size_t)std::max<int64_t>(n, 1), "peel prefixes"));
@@ -149,6 +151,10 @@ int peel_prepare(abcore_ctx *ctx) {
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
     ABC_TRY(ctx->alloc(&w.alive, (size_t)std::max<int64_t>(n, 1), "membership bytes"));
+    w.flag_blocks = cascade_grid(ctx);
+    ABC_TRY(ctx->alloc(&w.flags, (size_t)w.flag_blocks * 32, "queue close flags"));
+    ABC_CU(cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (size_t)w.flag_blocks * 32, ctx->stream));
+    w.epoch = 0;
     ABC_CU(cudaMallocHost(&w.ctl_host, sizeof(PeelCtl) * CTL_RING));
     for (int i = 0; i < CTL_RING; ++i) w.pending[i] = false;
     w.next = 0;
@@ -168,6 +174,8 @@ void free_peel(abcore_ctx *ctx) {
     ctx->release(w.ctl);
     ctx->release(w.stage);
     ctx->release(w.alive);
+    ctx->release(w.flags);
+    w.flag_blocks = 0;
     if (w.ctl_host) cudaFreeHost(w.ctl_host);
     w.ctl_host = nullptr;
     for (int i = 0; i < CTL_RING; ++i) {
@@ -258,6 +266,11 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
+    a.flags = w.flags;
+    a.flag_first = 0;
+    a.flag_count = blocks;
+    if (++w.epoch == 0) w.epoch = 1;  // (a wrap could only meet flags 2^32 peels old)
+    a.epoch = w.epoch;
 
     SlotInfo &si = w.info[slot];
     si = SlotInfo{};

@@ -20,12 +20,24 @@
 namespace abc {
 
 constexpr unsigned long long EMPTY = ~0ull;
+// one close flag per block, each on its own 128-byte line
+constexpr int FLAG_STRIDE = 32;
 constexpr int MAX_GRAB = 32;
+
+// Per-warp buffer of fallen vertices waiting to be queued (see push_add).
+template <int CAP>
+struct PushBuf {
+    static_assert(CAP >= 64, "a flush must leave room for one warp's pushes");
+    int32_t y[CAP];  // vertex
+    int32_t n[CAP];  // its item count, | PUSH_FROM1 when its chunks start at index 1
+};
+constexpr int32_t PUSH_FROM1 = 1 << 30;
 
 struct WarpSmem {
     long long start[MAX_GRAB];  // first adjacency index of each grabbed item
     int excl[MAX_GRAB];         // exclusive prefix of item lengths
     int upper[MAX_GRAB];        // 1 if the item's row belongs to a U vertex
+    PushBuf<256> push;
 };
 
 struct LaneStats {
@@ -57,29 +69,58 @@ __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper
 // cp[x].y (the full degree when its layer's counts came from the full rows).
 __device__ __forceinline__ int row_len_of(const PeelArgs &a, int32_t y) { return __ldcg(&a.plen[y]); }
 
-// Warp-collective: lanes with `want` queue vertex y as nch items (nch may be 0).
-__device__ __forceinline__ void warp_push(const PeelArgs &a, bool want, int32_t y, int nch, LaneStats &ls) {
-    const unsigned pm = __ballot_sync(ABC_FULL, want);
-    if (pm == 0) return;
+// Pushes are buffered per warp and queued in bulk: one atomicAdd on the queue's tail reserves
+// the slots of many fallen vertices at once (tail is a single hot word that every pusher hits).
+//
+// Warp-collective: queue the buffered vertices (pb.*[0, pc)) and empty the buffer.
+template <int CAP>
+__device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, int &pc) {
+    if (pc == 0) return;
+    __syncwarp();
     const int lane = threadIdx.x & 31;
-    if (!want) nch = 0;
-    else {
-        ls.pushes++;
-        if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
-    }
-    const int incl = warp_incl_scan(nch);
+    int mine = 0;
+    for (int i = lane; i < pc; i += 32) mine += pb.n[i] & (PUSH_FROM1 - 1);
+    const int incl = warp_incl_scan(mine);
     const int total = __shfl_sync(ABC_FULL, incl, 31);
-    if (total == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&a.ctl->tail, (unsigned long long)total);
     base = __shfl_sync(ABC_FULL, base, 0);
     if (base + (unsigned long long)total > (unsigned long long)a.qcap) {
         if (lane == 0) set_error(&a.ctl->err, ABCORE_ENOMEM);
-        return;
+    } else {
+        unsigned long long pos = base + (unsigned long long)(incl - mine);
+        for (int i = lane; i < pc; i += 32) {
+            const unsigned long long hi = (unsigned long long)(uint32_t)pb.y[i] << 32;
+            const int nch = pb.n[i] & (PUSH_FROM1 - 1);
+            const unsigned c0 = (pb.n[i] & PUSH_FROM1) ? 1u : 0u;
+            for (int c = 0; c < nch; ++c) st_relaxed(&a.q[pos + c], hi | (c0 + (unsigned)c));
+            pos += (unsigned long long)nch;
+        }
     }
-    unsigned long long pos = base + (unsigned long long)(incl - nch);
-    for (int i = 0; i < nch; ++i)
-        st_relaxed(&a.q[pos + i], ((unsigned long long)(uint32_t)y << 32) | (unsigned)i);
+    __syncwarp();
+    pc = 0;
+}
+
+// Warp-collective: lanes with `want` queue nch items of vertex y, chunks [0, nch) (or [1, nch]
+// with `from1`); nch == 0 queues nothing. With `fallen`, y is a vertex that has just fallen (it
+// is counted, and its removal step recorded). Flushes when the buffer is nearly full.
+template <int CAP>
+__device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, int &pc, bool want, int32_t y, int nch,
+                                         LaneStats &ls, bool fallen = true, bool from1 = false) {
+    if (want && fallen) {
+        ls.pushes++;
+        if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+    }
+    const bool keep = want && nch > 0;
+    const unsigned pm = __ballot_sync(ABC_FULL, keep);
+    if (pm == 0) return;
+    if (keep) {
+        const int i = pc + __popc(pm & lanemask_lt());
+        pb.y[i] = y;
+        pb.n[i] = nch | (from1 ? PUSH_FROM1 : 0);
+    }
+    pc += __popc(pm);
+    if (pc > CAP - 32) push_flush(a, pb, pc);
 }
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
@@ -90,21 +131,30 @@ constexpr int ILP = 4;
 
 // Warp-collective: process the items held by the lanes (`it` == EMPTY: none), spreading the
 // row chunks' entries evenly over the lanes (warp-level load balancing over an exclusive scan).
+//
+// A vertex that falls during the cascade is queued as one item, chunk 0; whoever takes chunk 0
+// of a row longer than one chunk queues the row's other chunks. (The pusher would otherwise
+// have to read the fallen vertex's row length, one more dependent memory round trip per push.)
 __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long it, WarpSmem &sm,
                                               LaneStats &ls) {
     const int lane = threadIdx.x & 31;
     long long start = 0;
-    int len = 0, upper = 0;
+    int len = 0, upper = 0, more = 0;
+    int32_t x = 0;
     if (it != EMPTY) {
-        const int32_t x = (int32_t)(it >> 32);
+        x = (int32_t)(it >> 32);
         const int c = (int)(it & 0xffffffffu);
         const int rl = row_len_of(a, x);
         start = __ldg(&a.off[x]) + (long long)c * a.chunk;
         len = min(a.chunk, rl - c * a.chunk);
         if (len < 0) len = 0;
+        if (c == 0 && rl > a.chunk) more = chunks_of(rl, a.chunk) - 1;
         upper = x < a.nU;
         ls.items++;
     }
+    int pc = 0;
+    push_add(a, sm.push, pc, more > 0, x, more, ls, /*fallen=*/false, /*from1=*/true);
+    push_flush(a, sm.push, pc);
     const int incl = warp_incl_scan(len);
     const int L = __shfl_sync(ABC_FULL, incl, 31);
     sm.start[lane] = start;
@@ -138,15 +188,42 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
                 hit[u] = cand_of(a, y[u], thr[u] != 0, t) && (t > 0 || !a.skip_zero);
                 thr[u] = t;
             }
-            old[u] = hit[u] ? atomicSub(&a.cnt[y[u]], 1) : 0;
         }
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) old[u] = hit[u] ? atomicSub(&a.cnt[y[u]], 1) : 0;
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (hit[u]) ls.decs++;
-            const bool push = hit[u] && old[u] == thr[u];
-            warp_push(a, push, y[u], push ? chunks_of(row_len_of(a, y[u]), a.chunk) : 0, ls);
+            // the crossing decrement: y had a count of 1 or more, so its row is not empty
+            push_add(a, sm.push, pc, hit[u] && old[u] == thr[u], y[u], 1, ls);
         }
+        if (pc >= 32) push_flush(a, sm.push, pc);
     }
+    push_flush(a, sm.push, pc);
+    __syncwarp();
+}
+
+// `head` is set to CLOSED when the queue drains; a ticket grab that returns CLOSED or more ends
+// the holder's loop.
+constexpr unsigned long long CLOSED = 1ull << 62;
+
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The watcher closes a drained (or failed) queue: head moves to CLOSED, so no warp can take a
+// ticket any more, and every block of the launch (or chain) gets the closing epoch in its own
+// flag line. Warp-collective.
+__device__ __forceinline__ void close_queue(const PeelArgs &a) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) atomicExch(&a.ctl->head, CLOSED);
+    for (int i = lane; i < a.flag_count; i += 32)
+        st_relaxed_u32(a.flags + (size_t)(a.flag_first + i) * FLAG_STRIDE, a.epoch);
     __syncwarp();
 }
 
@@ -157,21 +234,27 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
 // `head` (k grows with the visible backlog), and lane l owns slot base + l. Pushers fill slots
 // in reservation order, so a ticket below `tail` is filled soon. Items are processed as soon as
 // any lane's slot is filled; lanes still waiting keep their tickets (holding items while
-// waiting could starve the very pushes that fill the remaining slots). When done == tail
-// nothing is in flight, so nothing can be queued any more: every ticket at or above tail will
-// never be filled and its holder leaves. (done is read before tail; both only grow and
-// done <= tail, so equality at those two reads proves the queue drained.)
+// waiting could starve the very pushes that fill the remaining slots).
 //
-// An idle warp reads done and tail only on every 16th idle poll (the block's first warp on every
-// one) and publishes a verdict in shared memory for the rest of its block; otherwise it polls
-// only its own slots. (Thousands of idle warps polling the two shared words on every iteration
-// would saturate the L2 slice that also serves the pushers' atomics.)
-__device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, LaneStats &ls, int grab_div) {
-    __shared__ volatile int s_verdict;  // 0 running, 1 drained, 3 error
+// Termination: one warp of the launch (the watcher) reads done and tail while it is idle.
+// done == tail means nothing is in flight, so nothing can be queued any more (done is read
+// before tail; both only grow and done <= tail, so equality at those two reads proves the queue
+// drained). The watcher then closes the queue (close_queue). Each block's first warp polls only
+// its block's own flag line, and every warp that learns of the close (from the flag, from a
+// CLOSED grab, or from an error) passes the news to the block's other warps in shared memory;
+// tickets still waiting are at or above tail and were never filled, so their slots are empty
+// and can simply be abandoned. Thousands of idle warps thus never poll the words that the
+// pushers' atomics need. Every waiting warp still checks the error word, and whether `done`
+// moves, on every 64th idle poll: with no progress for timeout_ns it records ABCORE_ETIMEDOUT and
+// leaves. A watcher that sees an error closes the queue so that everyone leaves promptly.
+__device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, LaneStats &ls, int grab_div,
+                                            bool watcher) {
+    __shared__ volatile uint32_t s_closed;  // == a.epoch once this block learnt of the close
     const int lane = threadIdx.x & 31;
     const bool leader = (threadIdx.x >> 5) == 0;
-    if (threadIdx.x == 0) s_verdict = 0;
+    if (threadIdx.x == 0) s_closed = 0;
     __syncthreads();
+    const uint32_t *myflag = a.flags + (size_t)blockIdx.x * FLAG_STRIDE;
     unsigned long long idle_since = now_ns(), last_done = ~0ull;
     int st = 2;  // this lane's ticket: 0 waiting, 2 none
     unsigned long long my = 0;
@@ -179,24 +262,38 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
     unsigned idle_polls = 0;
     for (;;) {
         if (__ballot_sync(ABC_FULL, st == 0) == 0) {  // no ticket held: take new ones
-            // lane 0 reads the block's verdict for the whole warp, so the warp stays converged
-            const int sv = __shfl_sync(ABC_FULL, lane == 0 ? s_verdict : 0, 0);
-            if (sv != 0) return sv == 1 ? 1 : 0;
             unsigned long long base = 0;
-            int k = 1;
+            int k = 1, closed = 0;
             if (lane == 0) {
-                const unsigned long long t = ld_relaxed(&a.ctl->tail);
-                const unsigned long long h = ld_relaxed(&a.ctl->head);
-                if (t > h) {
-                    const unsigned long long kk = (t - h) / (unsigned long long)grab_div;
-                    k = (int)(kk < 1 ? 1 : (kk > MAX_GRAB ? MAX_GRAB : kk));
+                if (s_closed == a.epoch) {
+                    closed = 1;
+                } else {
+                    const unsigned long long t = ld_relaxed(&a.ctl->tail);
+                    const unsigned long long h = ld_relaxed(&a.ctl->head);
+                    if (t > h) {
+                        const unsigned long long kk = (t - h) / (unsigned long long)grab_div;
+                        k = (int)(kk < 1 ? 1 : (kk > MAX_GRAB ? MAX_GRAB : kk));
+                    }
+                    base = atomicAdd(&a.ctl->head, (unsigned long long)k);
+                    if (base >= CLOSED) closed = 1;
+                    else if (base + (unsigned long long)k > (unsigned long long)a.qcap) {
+                        // tickets past the end of the queue: only an overflowed queue gets here
+                        set_error(&a.ctl->err, ABCORE_ENOMEM);
+                        closed = 2;
+                    }
+                    if (closed) closed |= ld_relaxed_i32(&a.ctl->err) != 0 ? 2 : 0;
                 }
-                base = atomicAdd(&a.ctl->head, (unsigned long long)k);
+            }
+            closed = __shfl_sync(ABC_FULL, closed, 0);
+            if (closed) {
+                if (watcher && (closed & 2)) close_queue(a);
+                if (lane == 0) s_closed = a.epoch;  // tell the block's waiting warps
+                return (closed & 2) ? 0 : 1;
             }
             base = __shfl_sync(ABC_FULL, base, 0);
             k = __shfl_sync(ABC_FULL, k, 0);
             my = base + (unsigned long long)lane;
-            st = (lane < k && my < (unsigned long long)a.qcap) ? 0 : 2;
+            st = lane < k ? 0 : 2;
         }
         unsigned long long it = EMPTY;
         if (st == 0) {
@@ -216,14 +313,21 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
             sleep_ns = 32;
             continue;
         }
-        // nothing arrived: drained, error, or keep waiting
-        int verdict = __shfl_sync(ABC_FULL, lane == 0 ? s_verdict : 0, 0);
-        if (verdict == 0 && (leader || (++idle_polls & 15) == 0)) {
-            if (lane == 0) {
+        // nothing arrived: has the queue closed (drained, or failed)?
+        int verdict = 0;  // 0 keep waiting, 1 drained, 3 error
+        if (lane == 0) {
+            if (s_closed == a.epoch) {
+                verdict = 1;
+            } else if (leader && ld_relaxed_u32(myflag) == a.epoch) {
+                s_closed = a.epoch;
+                verdict = 1;
+            }
+            if (verdict == 1 && ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
+            if (verdict == 0 && (watcher || (++idle_polls & 63) == 0)) {
                 const unsigned long long d = ld_acquire(&a.ctl->done);
                 const unsigned long long tcur = ld_acquire(&a.ctl->tail);
-                if (d == tcur) verdict = 1;
-                else if (ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
+                if (ld_relaxed_i32(&a.ctl->err) != 0) verdict = 3;
+                else if (watcher && d == tcur) verdict = 1;
                 else if (d != last_done) {  // the device is making progress: restart the clock
                     last_done = d;
                     idle_since = now_ns();
@@ -231,16 +335,13 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
                     set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
                     verdict = 3;
                 }
-                if (verdict != 0) s_verdict = verdict;
             }
-            verdict = __shfl_sync(ABC_FULL, verdict, 0);
         }
-        if (verdict == 3) return 0;
-        if (verdict == 1) {
-            // drained: nothing can be queued any more, so every ticket still waiting is at or
-            // above tail and will never be filled (a ticket below tail would be filled and,
-            // being only its holder's to process, would keep done below tail)
-            return 1;
+        verdict = __shfl_sync(ABC_FULL, verdict, 0);
+        if (verdict != 0) {
+            if (watcher) close_queue(a);
+            if (lane == 0) s_closed = a.epoch;  // tell the block's waiting warps
+            return verdict == 1 ? 1 : 0;
         }
         __nanosleep(sleep_ns);
         if (sleep_ns < 256) sleep_ns <<= 1;
@@ -251,10 +352,12 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
 // Per layer, the count is either the row prefix below the other layer's candidate boundary
 // (binary search in the sorted row) or the full degree (to be corrected by stream_range).
 // Candidates already below their bound are queued. Warp-collective; `t0` is warp-aligned.
-__device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_t nthreads, LaneStats &ls,
-                                           unsigned long long &probes, unsigned long long &inits) {
+template <int CAP>
+__device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, int64_t t0, int64_t nthreads,
+                                           LaneStats &ls, unsigned long long &probes, unsigned long long &inits) {
     const int64_t P = (int64_t)a.pU + a.pV;
     const int lane = threadIdx.x & 31;
+    int pc = 0;
     for (int64_t b = t0 - lane; b < P; b += nthreads) {
         const int64_t i = b + lane;
         bool viol = false;
@@ -292,10 +395,11 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, int64_t t0, int64_
             inits++;
             const int32_t thr = upper ? a.thrU : a.thrV;
             viol = len < thr;
-            nch = chunks_of(len, a.chunk);
+            nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
         }
-        warp_push(a, viol, x, nch, ls);
+        push_add(a, pb, pc, viol, x, nch, ls);
     }
+    push_flush(a, pb, pc);
 }
 
 // One adjacency entry y of an initial violator's row: lower y's count if y is a candidate that
@@ -360,9 +464,11 @@ __device__ __forceinline__ void stream_range(const PeelArgs &a, int64_t sa, int6
 // After the violator stream: queue the candidates counted by degree whose count fell below
 // their bound (hubs and searched layers were queued by init_range). Warp-collective; `t0` is
 // this thread's index among nthreads.
-__device__ __forceinline__ void scan_range(const PeelArgs &a, int64_t t0, int64_t nthreads, LaneStats &ls,
-                                           unsigned long long &scanned) {
+template <int CAP>
+__device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, int64_t t0, int64_t nthreads,
+                                           LaneStats &ls, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
+    int pc = 0;
     const int64_t u0 = a.searchU ? a.pU : a.hubcutU;  // U ids [u0, pU) counted by degree
     const int64_t v0 = a.searchV ? a.pV : a.hubcutV;  // V ids nU + [v0, pV)
     const int64_t nu = a.pU - u0, total = nu + (a.pV - v0);
@@ -375,11 +481,12 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, int64_t t0, int64_
             x = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
             const int c = __ldcg(&a.cnt[x]);
             viol = c < (x < a.nU ? a.thrU : a.thrV);
-            if (viol) nch = chunks_of(__ldcg(&a.plen[x]), a.chunk);
+            if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
             scanned++;
         }
-        warp_push(a, viol, x, nch, ls);
+        push_add(a, pb, pc, viol, x, nch, ls);
     }
+    push_flush(a, pb, pc);
 }
 
 __device__ __forceinline__ void flush_stats(const PeelArgs &a, LaneStats &ls) {
