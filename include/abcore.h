@@ -150,6 +150,20 @@ int abcore_sync(abcore_ctx *ctx);
 int abcore_query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta,
                       uint8_t *in_core);
 
+/* ---- connected components (Section 5: the component labels GFQ keeps) ------------------- */
+
+/* Connected components of the current graph (served updates included). label_u[nU] and
+ * label_v[nV] receive each vertex's component label: the smallest unified caller id in its
+ * component, where U vertex u is u and V vertex v is nU + v (so labels do not depend on how
+ * the library numbers vertices inside). An isolated vertex is a component of its own.
+ * *n_components (may be NULL) receives the number of components. Computed on the device by
+ * lock-free union-find over the edges. While serving, the loop keeps the component forest
+ * current: an insert unites two components at once; after a delete, which may split one, this
+ * call recomputes the forest from the current graph. The call waits until every submitted
+ * update has been applied. Errors: EINVAL (NULL label array), ENOTLOADED, ENOMEM. */
+int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64_t *n_components,
+                      uint32_t flags);
+
 /* ---- serving: continuously batched update/query stream ---------------------------------- */
 
 typedef struct {

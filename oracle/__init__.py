@@ -13,6 +13,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   nested property; the paper's worked examples.
 * ``core_numbers``  -- pinned against networkx.core_number.
 * ``replay``        -- pinned: brute force on tiny update streams.
+* ``components``    -- pinned: scipy.sparse.csgraph.connected_components on random graphs,
+  closed forms (no edges, complete bipartite, perfect matchings, paths).
 """
 
 import ctypes
@@ -52,6 +54,9 @@ def _load():
         lib.orc_peel_csr.argtypes = [ctypes.c_int32, ctypes.c_int32, _i64p, _i32p,
                                      ctypes.c_int32, ctypes.c_int32, _u8p]
         lib.orc_core_numbers.argtypes = [ctypes.c_int32, ctypes.c_int32, _i64p, _i32p, _i32p]
+        lib.orc_components.argtypes = [ctypes.c_int32, ctypes.c_int32, _i64p, _i32p, _i32p,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_components.restype = ctypes.c_int
         lib.orc_replay.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _i32p, _i32p,
                                    ctypes.c_int64, _i8p, _i32p, _i32p, _i32p, _i32p, _u8p,
                                    _i8p, _u8p, _i32p]
@@ -135,3 +140,16 @@ def replay(nU, nV, eu, ev, op, qu, qv, alpha, beta, check=None):
     if rc != 0:
         raise OracleError(rc, "replay")
     return answer[:nops], bits[:nops], status[:nops]
+
+
+def components(nU, nV, off, adj):
+    """(labels int32[nU+nV], count): each vertex's component labelled by its smallest unified id."""
+    label = np.zeros(max(nU + nV, 1), dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    if adj.size == 0:
+        adj = np.zeros(1, dtype=np.int32)
+    nc = ctypes.c_int64(0)
+    rc = _load().orc_components(nU, nV, np.ascontiguousarray(off, dtype=np.int64), adj, label, ctypes.byref(nc))
+    if rc != 0:
+        raise OracleError(rc, "components")
+    return label[: nU + nV], int(nc.value)

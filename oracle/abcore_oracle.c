@@ -18,6 +18,9 @@
  *   orc_replay        - the on-the-fly query problem (Section 3): apply edge updates in order,
  *                       and at the requested steps peel the updated graph from scratch and
  *                       report whether both endpoints of the update lie in the target core.
+ *   orc_components    - connected components of the graph (the labels GFQ keeps, Section 5),
+ *                       by breadth-first search from each unvisited vertex in increasing id
+ *                       order, so each component is labelled by its smallest unified id.
  *
  * Return codes match the library's: 0 ok, -1 invalid argument, -3 out of memory,
  * -4 edge already present, -5 edge absent.
@@ -262,4 +265,40 @@ done:
     if (g) for (int64_t z = 0; z < n; ++z) free(g[z].a);
     free(g); free(rows); free(len); free(alive);
     return rc;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Connected components: breadth-first search from every vertex not yet reached, taking start */
+/* vertices in increasing unified id; every vertex reached gets the start's id as its label,  */
+/* which is then the smallest id in its component. Returns the component count in *ncomp.     */
+/* ---------------------------------------------------------------------------------------- */
+int orc_components(int32_t nU, int32_t nV, const int64_t *off, const int32_t *adj, int32_t *label,
+                   int64_t *ncomp)
+{
+    if (nU < 0 || nV < 0) return ORC_EINVAL;
+    int64_t n = (int64_t)nU + nV;
+    int32_t *queue = malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    if (!queue) return ORC_ENOMEM;
+    for (int64_t x = 0; x < n; ++x) label[x] = -1;
+    int64_t count = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        if (label[s] >= 0) continue;
+        count++;
+        int64_t head = 0, tail = 0;
+        label[s] = (int32_t)s;
+        queue[tail++] = (int32_t)s;
+        while (head < tail) {
+            int32_t x = queue[head++];
+            for (int64_t i = off[x]; i < off[x + 1]; ++i) {
+                int32_t y = adj[i];
+                if (label[y] < 0) {
+                    label[y] = (int32_t)s;
+                    queue[tail++] = y;
+                }
+            }
+        }
+    }
+    free(queue);
+    *ncomp = count;
+    return ORC_OK;
 }

@@ -137,6 +137,19 @@ class ABCore:
     def sync(self):
         self._check(abi.abcore_sync(self._h))
 
+    def components(self, out_u=None, out_v=None):
+        """Component labels (int32, the smallest unified caller id in each component) and the
+        number of components; device tensors unless outputs are given."""
+        torch = _torch()
+        if out_u is None:
+            out_u = torch.empty(self.nU, dtype=torch.int32, device="cuda:%d" % self.device)
+            out_v = torch.empty(self.nV, dtype=torch.int32, device="cuda:%d" % self.device)
+        pu, fl = self._ptr(out_u)
+        pv, _ = self._ptr(out_v)
+        nc = ctypes.c_int64(0)
+        self._check(abi.abcore_components(self._h, pu, pv, ctypes.byref(nc), fl))
+        return out_u, out_v, int(nc.value)
+
     def query_edge(self, u, v, op, alpha, beta):
         r = ctypes.c_uint8(0)
         self._check(abi.abcore_query_edge(self._h, int(u), int(v), int(op), int(alpha), int(beta), ctypes.byref(r)))

@@ -220,6 +220,38 @@ int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, cons
     return rc;
 }
 
+int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64_t *n_components,
+                      uint32_t flags) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    const Graph &g = ctx->g;
+    if ((g.nU > 0 && !label_u) || (g.nV > 0 && !label_v)) return ctx->fail(ABCORE_EINVAL, "NULL label array");
+    ABC_TRY(peel_finish(ctx));
+    if (g.n() == 0) {
+        if (n_components) *n_components = 0;
+        return ABCORE_OK;
+    }
+    int32_t *du = label_u, *dv = label_v, *tmp = nullptr;
+    if (!ptr_on_device(flags)) {
+        ABC_TRY(ctx->alloc(&tmp, (size_t)g.n(), "component labels"));
+        du = tmp;
+        dv = tmp + g.nU;
+    }
+    int rc = ctx->serve ? serve_components(ctx, du, dv, n_components) : components_compute(ctx, du, dv, n_components);
+    if (!rc && tmp) {
+        cudaError_t e = cudaSuccess;
+        if (g.nU) e = cudaMemcpyAsync(label_u, du, sizeof(int32_t) * g.nU, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && g.nV)
+            e = cudaMemcpyAsync(label_v, dv, sizeof(int32_t) * g.nV, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = ctx->cuda_fail(e, "component label download");
+    }
+    ctx->release(tmp);
+    return rc;
+}
+
 int abcore_sync(abcore_ctx *ctx) {
     if (!ctx) return ABCORE_EINVAL;
     ABC_CU(cudaSetDevice(ctx->device));

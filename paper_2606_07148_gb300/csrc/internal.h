@@ -247,6 +247,12 @@ int serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out);
 int serve_stop(abcore_ctx *ctx);
 int serve_materialize(abcore_ctx *ctx);  // rebuild the CSR if served updates changed the graph
 void free_serve(abcore_ctx *ctx);
+int serve_components(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
+
+// components.cu -- connected components (union-find)
+int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st);
+int cc_emit(abcore_ctx *ctx, int32_t *parent, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp, cudaStream_t st);
+int components_compute(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
 
 static inline int64_t cnt_ge(const std::vector<int64_t> &t, int32_t thr) {
     if (thr <= 0) return t.empty() ? 0 : t[0];

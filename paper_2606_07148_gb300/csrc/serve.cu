@@ -43,6 +43,7 @@
 #include <thread>
 #include <vector>
 
+#include "cc_core.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -94,6 +95,8 @@ struct ServeArgs {
     unsigned long long *progress_dev;   // device: requests processed, per target
     unsigned long long *exit_at;        // device: ~0, or the request count every block stops at
     int *err;                           // device: first error
+    int32_t *comp;                      // component union-find over the current graph
+    int *comp_stale;                    // set once a delete may have split a component
     int32_t slots;
     unsigned long long idle_ns, timeout_ns;
 };
@@ -472,6 +475,12 @@ __global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
         int bits = 0;
         const int st = process_update(A, S, r.op, x, y, ep, &bits);
         if (threadIdx.x == 0) {
+            // component labels (kept by the first target's block): an insert joins the two
+            // components; a delete may split one, which the next label request recomputes
+            if (t == 0 && st == ABCORE_OK) {
+                if (r.op == ABCORE_INSERT) abc::cc_unite(A.comp, x, y);
+                else *A.comp_stale = 1;
+            }
             if (r.target == t) {
                 abcore_resp *o = A.resp + (k % (unsigned long long)A.slots);
                 o->seq = k;
@@ -565,6 +574,16 @@ __global__ void k_collect_edges(const int64_t *off, const int32_t *adj, const in
     }
 }
 
+// Union the inserted edges of the current graph (view of target 0) into a component forest.
+__global__ void k_cc_inserted(int32_t nU, TargetDev S, int32_t *parent) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nU; x += (int64_t)gridDim.x * blockDim.x) {
+        for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next) {
+            const DNode d = S.dpool[nd];
+            if (d.alive) abc::cc_unite(parent, (int32_t)x, d.y);
+        }
+    }
+}
+
 }  // namespace
 
 struct ServeState {
@@ -583,6 +602,8 @@ struct ServeState {
     unsigned long long *d_resp_seq = nullptr, *d_ctl = nullptr;
     unsigned long long *d_progress = nullptr, *d_exit_at = nullptr;
     int *d_err = nullptr;
+    int32_t *d_comp = nullptr;          // component union-find (see k_serve)
+    int *d_comp_stale = nullptr;
     unsigned long long next_seq = 0, consumed = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t loop_done = nullptr;
@@ -631,6 +652,8 @@ static int launch_loop(abcore_ctx *ctx, ServeState *s) {
     A.progress_dev = s->d_progress;
     A.exit_at = s->d_exit_at;
     A.err = s->d_err;
+    A.comp = s->d_comp;
+    A.comp_stale = s->d_comp_stale;
     A.slots = s->slots;
     A.idle_ns = 200ull * 1000000ull;
     A.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
@@ -673,6 +696,8 @@ static void release_serve(abcore_ctx *ctx, ServeState *s) {
     ctx->release(s->d_progress);
     ctx->release(s->d_exit_at);
     ctx->release(s->d_err);
+    ctx->release(s->d_comp);
+    ctx->release(s->d_comp_stale);
     if (s->h_req) cudaFreeHost(s->h_req);
     if (s->h_resp) cudaFreeHost(s->h_resp);
     if (s->h_resp_seq) cudaFreeHost(s->h_resp_seq);
@@ -773,6 +798,11 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
     ABC_TRY(ctx->alloc(&s->d_exit_at, 1, "serve exit"));
     ABC_CU(cudaMemsetAsync(s->d_progress, 0, sizeof(unsigned long long) * nt, ctx->stream));
     ABC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), ctx->stream));
+    // component labels of the graph as loaded; the serving loop keeps them current
+    ABC_TRY(ctx->alloc(&s->d_comp, (size_t)std::max<int64_t>(n, 1), "serve components"));
+    ABC_TRY(ctx->alloc(&s->d_comp_stale, 1, "serve components"));
+    ABC_CU(cudaMemsetAsync(s->d_comp_stale, 0, sizeof(int), ctx->stream));
+    ABC_TRY(cc_hook_base(ctx, s->d_comp, nullptr, ctx->stream));
     const int64_t tomb_words = (2 * g.m + 31) / 32 + 1;
     for (int32_t t = 0; t < nt; ++t) {
         TargetDev T{};
@@ -926,4 +956,32 @@ int query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int
         return ctx->fail(resp.status, resp.status == ABCORE_EEXIST ? "insert: edge already present"
                                                                    : "delete: edge not present");
     return ABCORE_OK;
+}
+
+// Component labels of the current graph while serving: wait until every submitted update has
+// been applied, recompute the forest from the current graph if a delete may have split a
+// component (the paper re-runs the components of the affected component; this re-runs them
+// over the graph, on demand), then name the components.
+int serve_components(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp) {
+    ServeState *s = ctx->serve;
+    const auto t0 = std::chrono::steady_clock::now();
+    while (min_progress(s) < s->next_seq) {
+        ABC_TRY(check_device_error(ctx, s));
+        ABC_TRY(ensure_loop(ctx, s));
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(ctx->prm.timeout_ms * 4))
+            return ctx->fail(ABCORE_ETIMEDOUT, "components: served updates did not finish");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    ABC_TRY(check_device_error(ctx, s));
+    int stale = 0;
+    ABC_CU(cudaMemcpyAsync(&stale, s->d_comp_stale, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    if (stale) {
+        ABC_TRY(cc_hook_base(ctx, s->d_comp, s->tdev[0].tomb, ctx->stream));
+        k_cc_inserted<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(ctx->g.nU, s->tdev[0], s->d_comp);
+        ctx->stats.launches++;
+        ABC_CU(cudaGetLastError());
+        ABC_CU(cudaMemsetAsync(s->d_comp_stale, 0, sizeof(int), ctx->stream));
+    }
+    return cc_emit(ctx, s->d_comp, d_lab_u, d_lab_v, ncomp, ctx->stream);
 }

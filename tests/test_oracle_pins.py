@@ -335,3 +335,45 @@ def test_replay_paper_example1_insert():
     ev = np.array([e[1] for e in edges], dtype=np.int32)
     ans, bits, status = oracle.replay(nU, nV, eu, ev, [0], [4], [2], [1], [5])
     assert ans.tolist() == [1] and bits.tolist() == [3] and status.tolist() == [0]
+
+
+# ------------------------------------------------------------------------------------------
+# Connected components (the labels GFQ keeps, Section 5)
+# ------------------------------------------------------------------------------------------
+def _components_edges(nU, nV, edges):
+    eu = np.array([e[0] for e in edges], dtype=np.int32)
+    ev = np.array([e[1] for e in edges], dtype=np.int32)
+    off, adj = oracle.build_csr(nU, nV, eu, ev)
+    return oracle.components(nU, nV, off, adj)
+
+
+def test_components_match_scipy():
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    rng = random.Random(23)
+    for _ in range(40):
+        nU, nV = rng.randint(0, 40), rng.randint(0, 40)
+        edges = _random_graph(rng, nU, nV, rng.random() * 0.08)
+        lab, nc = _components_edges(nU, nV, edges)
+        n = nU + nV
+        rows = [u for u, v in edges] + [nU + v for u, v in edges]
+        cols = [nU + v for u, v in edges] + [u for u, v in edges]
+        A = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+        k, sl = connected_components(A, directed=False)
+        assert nc == k
+        # same partition, and each label is the smallest id of its component
+        for c in range(k):
+            members = np.nonzero(sl == c)[0]
+            assert set(lab[members].tolist()) == {int(members.min())}
+
+
+def test_components_closed_forms():
+    lab, nc = _components_edges(3, 4, [])                        # no edges: every vertex alone
+    assert nc == 7 and list(lab) == list(range(7))
+    lab, nc = _components_edges(3, 4, [(u, v) for u in range(3) for v in range(4)])
+    assert nc == 1 and set(lab.tolist()) == {0}                  # complete bipartite
+    lab, nc = _components_edges(5, 5, [(i, i) for i in range(5)])
+    assert nc == 5 and list(lab) == [0, 1, 2, 3, 4, 0, 1, 2, 3, 4]   # perfect matching
+    # path u0 - v0 - u1 - v1 - u2 plus an isolated v2
+    lab, nc = _components_edges(3, 3, [(0, 0), (1, 0), (1, 1), (2, 1)])
+    assert nc == 2 and list(lab) == [0, 0, 0, 0, 0, 5]
