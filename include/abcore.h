@@ -128,6 +128,20 @@ int abcore_load_csr(abcore_ctx *ctx, int32_t nU, int32_t nV,
 int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta,
                    uint8_t *mask_u, uint8_t *mask_v, uint32_t flags);
 
+/* Core numbers (Definition 2: the largest k with the vertex in the (k, k)-core) of every vertex,
+ * in the caller's ids: core_u[nU], core_v[nV]; *max_core (may be NULL) receives the largest.
+ * The first call after a graph is loaded (or changed by served updates) runs the preprocessing
+ * of Algorithm 2 (GCC+) on the device: the core decomposition, then a second copy of the graph
+ * with each layer numbered by non-increasing core number (another CSR's worth of device
+ * memory). abcore_compute may then prune with Lemma 1: vertices with core < min(alpha, beta)
+ * are out, those with core >= max(alpha, beta) are in, and only the rest are peeled. The
+ * "algo" parameter decides: 0 (default) prunes a query only when that leaves fewer vertices to
+ * peel than the plain peel's degree prefixes; 1 never prunes; 2 always prunes, and prepares
+ * the core numbers itself on first use. Errors: EINVAL (NULL array), ENOTLOADED, ENOMEM,
+ * ETIMEDOUT. */
+int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32_t *max_core,
+                        uint32_t flags);
+
 /* Compute n cores at once (Lemma 1 and Algorithm 2 generalised: pairs sharing alpha are peeled
  * as one chain of increasing beta, each core seeded from the one containing it). Pair i is
  * (alphas[i], betas[i]); its masks are rows i of masks_u (n x nU, row-major) and masks_v
@@ -185,7 +199,10 @@ typedef struct {
 
 /* Start serving with n_targets (alpha, beta) targets and a request ring of ring_slots entries.
  * Updates are applied in submission order and every answer is the one the update would get
- * if requests were processed one at a time, so answers do not depend on timing or batching. */
+ * if requests were processed one at a time, so answers do not depend on timing or batching.
+ * Each target keeps its own device view of the updates; inserted edges live in a pool sized by
+ * the "serve_inserts" parameter (default 2^20 inserts, 32 bytes each per target): once it is
+ * full the loop stops with ABCORE_ENOMEM, reported by the next submit, poll or stop. */
 int abcore_serve_start(abcore_ctx *ctx, const int32_t *target_alphas, const int32_t *target_betas,
                        int32_t n_targets, int32_t ring_slots);
 

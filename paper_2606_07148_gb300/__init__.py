@@ -137,6 +137,18 @@ class ABCore:
     def sync(self):
         self._check(abi.abcore_sync(self._h))
 
+    def core_numbers(self, out_u=None, out_v=None):
+        """Core numbers (int32, Definition 2) and the largest; prepares the GCC+ pruned peel."""
+        torch = _torch()
+        if out_u is None:
+            out_u = torch.empty(self.nU, dtype=torch.int32, device="cuda:%d" % self.device)
+            out_v = torch.empty(self.nV, dtype=torch.int32, device="cuda:%d" % self.device)
+        pu, fl = self._ptr(out_u)
+        pv, _ = self._ptr(out_v)
+        mx = ctypes.c_int32(0)
+        self._check(abi.abcore_core_numbers(self._h, pu, pv, ctypes.byref(mx), fl))
+        return out_u, out_v, int(mx.value)
+
     def components(self, out_u=None, out_v=None):
         """Component labels (int32, the smallest unified caller id in each component) and the
         number of components; device tensors unless outputs are given."""

@@ -29,7 +29,7 @@ ABCORE_DELETE = 1
 
 EXPORTED = [
     "abcore_create", "abcore_destroy", "abcore_last_error", "abcore_load_edges", "abcore_load_csr",
-    "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_query_edge",
+    "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_core_numbers", "abcore_query_edge",
     "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
     "abcore_get_stats", "abcore_set_param", "abcore_graph_info", "abcore_export_csr",
     "abcore_compute_static",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB):
         "abcore_compute": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
         "abcore_compute_batch": ([_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
         "abcore_sync": ([_vp], ctypes.c_int),
+        "abcore_core_numbers": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32], ctypes.c_int),
         "abcore_components": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32], ctypes.c_int),
         "abcore_query_edge": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
@@ -134,6 +135,7 @@ abcore_compute = _fn("abcore_compute")
 abcore_compute_batch = _fn("abcore_compute_batch")
 abcore_sync = _fn("abcore_sync")
 abcore_components = _fn("abcore_components")
+abcore_core_numbers = _fn("abcore_core_numbers")
 abcore_query_edge = _fn("abcore_query_edge")
 abcore_serve_start = _fn("abcore_serve_start")
 abcore_serve_submit = _fn("abcore_serve_submit")

@@ -173,11 +173,16 @@ int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *mask_u
     if ((flags & ABCORE_ASYNC) && !dev) return ctx->fail(ABCORE_EINVAL, "ABCORE_ASYNC needs device pointers");
     if (ctx->serve) ABC_TRY(serve_materialize(ctx));
     if (g.n() == 0) return ABCORE_OK;
-    if (dev) return peel_compute(ctx, alpha, beta, mask_u, mask_v, !(flags & ABCORE_ASYNC));
+    if (ctx->prm.algo == 2 && !ctx->pr.ready) {
+        ABC_TRY(peel_finish(ctx));
+        ABC_TRY(prepare_pruning(ctx));
+    }
+    const bool pruned = prefer_pruned(ctx, alpha, beta);
+    if (dev) return peel_compute(ctx, alpha, beta, mask_u, mask_v, !(flags & ABCORE_ASYNC), pruned);
     ABC_TRY(peel_finish(ctx));
     ABC_TRY(peel_prepare(ctx));
     uint8_t *su = ctx->w.stage, *sv = ctx->w.stage + g.nU;
-    ABC_TRY(peel_compute(ctx, alpha, beta, su, sv, false));
+    ABC_TRY(peel_compute(ctx, alpha, beta, su, sv, false, pruned));
     if (g.nU) ABC_CU(cudaMemcpyAsync(mask_u, su, (size_t)g.nU, cudaMemcpyDeviceToHost, ctx->stream));
     if (g.nV) ABC_CU(cudaMemcpyAsync(mask_v, sv, (size_t)g.nV, cudaMemcpyDeviceToHost, ctx->stream));
     return peel_finish(ctx);
@@ -218,6 +223,29 @@ int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, cons
     ctx->release(du);
     ctx->release(dv);
     return rc;
+}
+
+int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32_t *max_core, uint32_t flags) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    const Graph &g = ctx->g;
+    if ((g.nU > 0 && !core_u) || (g.nV > 0 && !core_v)) return ctx->fail(ABCORE_EINVAL, "NULL core array");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(peel_finish(ctx));
+    if (g.n() == 0) {
+        if (max_core) *max_core = 0;
+        return ABCORE_OK;
+    }
+    ABC_TRY(prepare_pruning(ctx));
+    const cudaMemcpyKind kind = ptr_on_device(flags) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (g.nU) ABC_CU(cudaMemcpyAsync(core_u, ctx->pr.core_caller, sizeof(int32_t) * g.nU, kind, ctx->stream));
+    if (g.nV)
+        ABC_CU(cudaMemcpyAsync(core_v, ctx->pr.core_caller + g.nU, sizeof(int32_t) * g.nV, kind, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    if (max_core) *max_core = ctx->pr.maxcore;
+    return ABCORE_OK;
 }
 
 int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64_t *n_components,
@@ -358,6 +386,12 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "timing must be 0 or 1");
         ABC_TRY(abcore_sync(ctx));
         p.timing = (int)value;
+    } else if (k == "serve_inserts") {
+        if (value < 1 || value > (1 << 29)) return ctx->fail(ABCORE_EINVAL, "serve_inserts must be in [1, 2^29]");
+        p.serve_inserts = value;
+    } else if (k == "algo") {
+        if (value < 0 || value > 2) return ctx->fail(ABCORE_EINVAL, "algo must be 0 (auto), 1 (GCC) or 2 (GCC+)");
+        p.algo = (int)value;
     } else if (k == "reset_stats") {
         ABC_TRY(abcore_sync(ctx));
         const int32_t mode = ctx->stats.mode, grid = ctx->stats.grid_blocks;

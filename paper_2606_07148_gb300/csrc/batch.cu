@@ -70,48 +70,6 @@ struct BatchArgs {
     unsigned long long timeout_ns;
 };
 
-// Bounded barrier over the `G` blocks of one chain. The last block to arrive can run `fixup`
-// while every other block of the group waits. Returns false if the group saw an error.
-__device__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl, bool fixup, unsigned long long timeout_ns) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned *genp = bar + 32;
-        const unsigned gen = *genp;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == (unsigned)G - 1) {
-            atomicExch(bar, 0u);
-            if (fixup) {
-                // the cascade closed the queue: the tickets it voided, [tail, old head), were
-                // emptied by their holders, so the next step's tickets restart at tail
-                const unsigned long long t = abc::ld_relaxed(&ctl->tail);
-                atomicExch(&ctl->head, t);
-                atomicExch(&ctl->done, t);
-            }
-            __threadfence();
-            atomicAdd(bar + 32, 1u);
-        } else {
-            const unsigned long long t0 = abc::now_ns();
-            unsigned sl = 32;
-            while (*genp == gen) {
-                if (abc::now_ns() - t0 > timeout_ns) {
-                    abc::set_error(&ctl->err, ABCORE_ETIMEDOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(sl);
-                if (sl < 512) sl <<= 1;
-            }
-        }
-        __threadfence();
-        if (abc::ld_relaxed_i32(&ctl->err) != 0) ok = 0;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     __shared__ WarpSmem smem[BATCH_THREADS / 32];
     int c = 0;
@@ -159,21 +117,21 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     unsigned long long probes = 0, inits = 0, ents = 0, sdecs = 0;
 
     abc::init_range(a, smem[wib].push, t0, nthreads, ls, probes, inits);
-    if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+    if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     if (cd.ea > cd.sa || cd.eb > cd.sb) {
         const unsigned long long d0 = ls.decs;
         abc::stream_range(a, cd.sa, cd.ea, cd.sb, cd.eb, t0, nthreads, ls, ents);
         sdecs = ls.decs - d0;
         ls.decs = d0;
-        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         unsigned long long scanned = 0;
         abc::scan_range(a, smem[wib].push, t0, nthreads, ls, scanned);
-        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     }
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
     (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
-    if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+    if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     for (int j = 1; j < cd.nsteps; ++j) {
         const int32_t prev = a.thrV;
         a.thrV = B.betas[cd.beta_off + j];
@@ -195,9 +153,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
             abc::push_add(a, smem[wib].push, pc, viol, x, nch, ls);
         }
         abc::push_flush(a, smem[wib].push, pc);
-        if (!group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
-        if (!group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+        if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     }
 out:
     abc::flush_stats(a, ls);

@@ -327,6 +327,39 @@ __global__ void k_extract(const uint64_t *__restrict__ keys, int64_t m, uint64_t
     }
 }
 
+// Second ordering pass (build with a rank): position p of the degree order gets the key
+// (maxrank - rank) << 32 | p, so a stable sort orders by non-increasing rank, ties by degree
+// order.
+__global__ void k_rank_keys(const uint64_t *__restrict__ by_degree, int64_t n, int32_t base,
+                            const int32_t *__restrict__ rank, int32_t maxrank, uint64_t *__restrict__ keys) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t old = (int32_t)(by_degree[p] & 0xffffffffu);
+        keys[p] = ((uint64_t)(uint32_t)(maxrank - rank[base + old]) << 32) | (uint64_t)p;
+    }
+}
+
+__global__ void k_rank_finish(const uint64_t *__restrict__ by_rank, const uint64_t *__restrict__ by_degree,
+                              int64_t n, int32_t base, int32_t maxdeg, int32_t *__restrict__ new2old,
+                              int32_t *__restrict__ old2new, int32_t *__restrict__ degnew) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = (int64_t)(by_rank[q] & 0xffffffffu);
+        const uint64_t k = by_degree[p];
+        const int32_t old = (int32_t)(k & 0xffffffffu);
+        new2old[base + q] = old;
+        old2new[base + old] = base + (int32_t)q;
+        degnew[base + q] = maxdeg - (int32_t)(k >> 32);
+    }
+}
+
+// Caller-id edges of a CSR's U rows: (new2old[row], new2old[column]).
+__global__ void k_edges_of(const int32_t *__restrict__ rowid, const int32_t *__restrict__ adj, int64_t m,
+                           const int32_t *__restrict__ new2old, int32_t *__restrict__ eu, int32_t *__restrict__ ev) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        eu[i] = new2old[rowid[i]];
+        ev[i] = new2old[adj[i]];
+    }
+}
+
 // cnt_ge[t] for t in [0, maxdeg+1] from a layer's degrees sorted non-increasing.
 __global__ void k_cnt_ge(const int32_t *__restrict__ deg, int64_t nl, int32_t maxdeg,
                          int64_t *__restrict__ cnt_ge) {
@@ -404,8 +437,7 @@ int read_err(abcore_ctx *ctx, int *d_err, int *h_err) {
 
 }  // namespace
 
-void free_graph(abcore_ctx *ctx) {
-    Graph &g = ctx->g;
+void free_graph_of(abcore_ctx *ctx, Graph &g) {
     ctx->release(g.off);
     ctx->release(g.adj);
     ctx->release(g.new2old);
@@ -414,6 +446,11 @@ void free_graph(abcore_ctx *ctx) {
     g.loaded = false;
     g.nU = g.nV = 0;
     g.m = 0;
+}
+
+void free_graph(abcore_ctx *ctx) {
+    free_pruning(ctx);
+    free_graph_of(ctx, ctx->g);
 }
 
 int check_csr_offsets(abcore_ctx *ctx, int32_t nrows, const int64_t *d_off, int64_t m) {
@@ -473,11 +510,28 @@ int compare_edge_sets(abcore_ctx *ctx, int32_t nV, int64_t m, const int32_t *eu1
 int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64_t m,
                                   const int32_t *d_eu, const int32_t *d_ev) {
     free_graph(ctx);
-    Graph &g = ctx->g;
+    return build_graph(ctx, ctx->g, nU, nV, m, d_eu, d_ev, nullptr, 0);
+}
+
+int csr_edges(abcore_ctx *ctx, const Graph &g, int32_t *d_eu, int32_t *d_ev) {
+    int32_t *rowid = nullptr;
+    ABC_TRY(ctx->alloc(&rowid, (size_t)std::max<int64_t>(g.m, 1), "edge rows"));
+    int rc = expand_csr_to_edges(ctx, g.nU, g.off, g.adj, g.m, rowid);
+    if (!rc && g.m > 0) {
+        k_edges_of<<<grid_for(ctx, g.m), 256, 0, ctx->stream>>>(rowid, g.adj, g.m, g.new2old, d_eu, d_ev);
+        const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = ctx->cuda_fail(e, "edge list");
+    }
+    ctx->release(rowid);
+    return rc;
+}
+
+int build_graph(abcore_ctx *ctx, Graph &g, int32_t nU, int32_t nV, int64_t m, const int32_t *d_eu,
+                const int32_t *d_ev, const int32_t *d_rank, int32_t maxrank) {
     const int64_t n = (int64_t)nU + nV;
     int32_t *deg = nullptr, *degnew = nullptr;
     int *d_err = nullptr, *d_max = nullptr;
-    uint64_t *ka = nullptr, *kb = nullptr;
+    uint64_t *ka = nullptr, *kb = nullptr, *rk = nullptr;
     int64_t *cnt_ge = nullptr, *edges_ge = nullptr;
     int h_err = 0, h_max[2] = {0, 0};
     int rc = ABCORE_OK;
@@ -526,8 +580,19 @@ int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64
             k_relabel_keys<<<grid_for(ctx, nl), 256, 0, ctx->stream>>>(deg + base, nl, md, ka);
             uint64_t *sorted;
             STEP(radix_sort_u64(ctx, ka, kb, nl, 32, 32 + bits_for((int64_t)md + 1), &sorted));
-            k_relabel_finish<<<grid_for(ctx, nl), 256, 0, ctx->stream>>>(sorted, nl, base, md, g.new2old,
-                                                                         g.old2new, degnew);
+            if (!d_rank) {
+                k_relabel_finish<<<grid_for(ctx, nl), 256, 0, ctx->stream>>>(sorted, nl, base, md, g.new2old,
+                                                                             g.old2new, degnew);
+            } else {
+                // then by non-increasing rank, ties keeping the degree order
+                if (!rk) STEP(ctx->alloc(&rk, (size_t)std::max<int64_t>(std::max<int64_t>(nU, nV), 1) * 2, "rank keys"));
+                uint64_t *ra = rk, *rb = rk + std::max<int64_t>(nU, nV);
+                k_rank_keys<<<grid_for(ctx, nl), 256, 0, ctx->stream>>>(sorted, nl, base, d_rank, maxrank, ra);
+                uint64_t *sorted2;
+                STEP(radix_sort_u64(ctx, ra, rb, nl, 32, 32 + bits_for((int64_t)maxrank + 1), &sorted2));
+                k_rank_finish<<<grid_for(ctx, nl), 256, 0, ctx->stream>>>(sorted2, sorted, nl, base, md, g.new2old,
+                                                                          g.old2new, degnew);
+            }
         }
         STEP(exclusive_scan_i32(ctx, degnew, n, g.off));
         // rows of both layers, sorted by (row, column) in internal ranks
@@ -548,8 +613,9 @@ int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64
             goto fail;
         }
     }
-    // host tables: vertices and edges at or above each degree threshold, per layer
-    for (int layer = 0; layer < 2; ++layer) {
+    // host tables: vertices and edges at or above each degree threshold, per layer (a graph
+    // ordered by rank is not in degree order, and gets none)
+    for (int layer = 0; layer < 2 && !d_rank; ++layer) {
         const int64_t nl = layer == 0 ? nU : nV;
         const int32_t md = layer == 0 ? g.maxdegU : g.maxdegV;
         const int64_t base = layer == 0 ? 0 : nU;
@@ -569,7 +635,7 @@ int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64
     }
     ABC_CU(cudaGetLastError());
     ctx->release(deg); ctx->release(degnew); ctx->release(d_err); ctx->release(d_max);
-    ctx->release(ka); ctx->release(kb);
+    ctx->release(ka); ctx->release(kb); ctx->release(rk);
     g.nU = nU;
     g.nV = nV;
     g.m = m;
@@ -579,8 +645,8 @@ int build_graph_from_device_edges(abcore_ctx *ctx, int32_t nU, int32_t nV, int64
 fail:
     cudaStreamSynchronize(ctx->stream);
     ctx->release(deg); ctx->release(degnew); ctx->release(d_err); ctx->release(d_max);
-    ctx->release(ka); ctx->release(kb); ctx->release(cnt_ge); ctx->release(edges_ge);
-    free_graph(ctx);
+    ctx->release(ka); ctx->release(kb); ctx->release(rk); ctx->release(cnt_ge); ctx->release(edges_ge);
+    free_graph_of(ctx, g);
     return rc;
 #undef STEP
 }

@@ -50,6 +50,8 @@ struct PeelArgs {
     PeelCtl *ctl;
     int32_t nU, nV;
     int32_t pU, pV;          // candidate prefixes: U [0,pU), V [nU, nU+pV)
+    int32_t cU, cV;          // vertices below these (U [0,cU), V [nU, nU+cV)) are certain members:
+                             // never counted, decremented or removed (0 for the plain peel)
     int32_t thrU, thrV;      // alpha, beta
     int32_t chunk;           // adjacency entries per work item
     int32_t grab_div;        // queue items per grab = clamp(available / grab_div, 1, 32)
@@ -69,6 +71,8 @@ struct PeelArgs {
     // lvl[vertex * lvl_stride + lvl_col] (lvl == nullptr: no record)
     uint8_t *lvl;
     int32_t lvl_stride, lvl_col, step;
+    int32_t *corev;          // if set, a vertex queued during `step` gets corev[vertex] = step
+    unsigned long long *removed;  // if set, counts the vertices queued
     // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
     // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
     uint32_t *flags;
@@ -89,6 +93,10 @@ struct Params {
                                // 4 measured best on a 500M-edge graph (counts stay closer to L2)
     int debug_stall_slots = 0; // test hook: queue slots reserved but never written
     int timing = 0;            // 1: CUDA events around each launch, summed into stats.kernel_ms
+    int64_t serve_inserts = 1 << 20;  // inserted edges each served target can hold (ENOMEM beyond)
+    int algo = 0;              // abcore_compute: 0 GCC+ when core numbers are prepared and it has
+                               // fewer vertices to peel, else GCC; 1 always GCC; 2 always GCC+
+                               // (prepares core numbers on first use)
     int hub_degree = 256;      // candidates of at least this degree always count by search: the
                                // violator stream would hit each of them that many times, and
                                // atomics on one address serialise (0 = off)
@@ -138,6 +146,18 @@ struct PeelWork {
     uint32_t epoch = 0;            // last cascade epoch handed out
 };
 
+// Algorithm 2 (GCC+) preprocessing: core numbers (Definition 2) and a copy of the graph whose
+// layers are numbered by non-increasing core number, so that for thresholds dl <= dq the vertices
+// with core >= dq (certain members) and core >= dl (the only possible members) are prefixes.
+struct Pruning {
+    bool ready = false;
+    Graph gc;                                 // core-ordered graph (degree order breaks ties)
+    int32_t *core_caller = nullptr;           // [n] core number by unified caller id
+    std::vector<int64_t> coreU_ge, coreV_ge;  // vertices of each layer with core >= t, t = 0..maxcore+1
+    int32_t maxcore = 0;
+    float decomp_ms = 0.f, layout_ms = 0.f;   // time of the last preparation
+};
+
 struct BatchState;
 struct ServeState;
 
@@ -148,6 +168,7 @@ struct abcore_ctx {
     int num_sms = 0;
     std::string err;
     Graph g;
+    Pruning pr;
     PeelWork w;
     Params prm;
     abcore_stats stats{};
@@ -222,13 +243,24 @@ int expand_csr_to_edges(abcore_ctx *ctx, int32_t nU, const int64_t *d_off, const
 int check_csr_offsets(abcore_ctx *ctx, int32_t nrows, const int64_t *d_off, int64_t m);
 int compare_edge_sets(abcore_ctx *ctx, int32_t nV, int64_t m, const int32_t *eu1, const int32_t *ev1,
                       const int32_t *eu2, const int32_t *ev2);
-void free_graph(abcore_ctx *ctx);
+void free_graph(abcore_ctx *ctx);  // the loaded graph and everything derived from it
+void free_graph_of(abcore_ctx *ctx, Graph &g);
+// Build `g` from m distinct caller-id edges; each layer numbered by non-increasing degree, or, with
+// d_rank (per unified caller id, values 0..maxrank), by non-increasing rank with ties in degree order.
+int build_graph(abcore_ctx *ctx, Graph &g, int32_t nU, int32_t nV, int64_t m, const int32_t *d_eu,
+                const int32_t *d_ev, const int32_t *d_rank, int32_t maxrank);
+int csr_edges(abcore_ctx *ctx, const Graph &g, int32_t *d_eu, int32_t *d_ev);  // caller-id edge list
+
+// coredecomp.cu -- core numbers and the GCC+ layout
+int prepare_pruning(abcore_ctx *ctx);
+void free_pruning(abcore_ctx *ctx);
 
 // peel.cu -- single (alpha, beta)-core
 int peel_prepare(abcore_ctx *ctx);
 int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
-                 bool sync_and_check);
+                 bool sync_and_check, bool pruned = false);
 int peel_finish(abcore_ctx *ctx);
+bool prefer_pruned(const abcore_ctx *ctx, int32_t alpha, int32_t beta);
 void free_peel(abcore_ctx *ctx);
 int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, int32_t pV);
 int cascade_grid(abcore_ctx *ctx);

@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
 }
 
 __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
-    if (x < a.nU) return x < a.pU && __ldcg(&a.cnt[x]) >= a.thrU;
-    return x < a.nU + a.pV && __ldcg(&a.cnt[x]) >= a.thrV;
+    if (x < a.nU) return x < a.pU && (x < a.cU || __ldcg(&a.cnt[x]) >= a.thrU);
+    return x < a.nU + a.pV && (x < a.nU + a.cV || __ldcg(&a.cnt[x]) >= a.thrV);
 }
 
 __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
@@ -219,17 +219,40 @@ int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, in
     return (sU ? 1 : 0) | (sV ? 2 : 0);
 }
 
-int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
-                 bool sync_and_check) {
+// With core numbers prepared, is the pruned peel (GCC+) the cheaper one? GCC+ initialises and
+// peels the vertices with core in [min(alpha, beta), max(alpha, beta)); the plain peel those
+// meeting their bound on full degree. Each side's vertex count stands for its cost: equal
+// bounds leave GCC+ nothing to peel, while far-apart bounds can leave it far more vertices than
+// the degree prefixes hold.
+bool prefer_pruned(const abcore_ctx *ctx, int32_t alpha, int32_t beta) {
+    if (!ctx->pr.ready || ctx->prm.algo == 1) return false;
+    if (ctx->prm.algo == 2) return true;
+    const Pruning &p = ctx->pr;
     const Graph &g = ctx->g;
+    const int32_t dl = std::min(alpha, beta), dq = std::max(alpha, beta);
+    const int64_t unc = (cnt_ge(p.coreU_ge, dl) - cnt_ge(p.coreU_ge, dq)) + (cnt_ge(p.coreV_ge, dl) - cnt_ge(p.coreV_ge, dq));
+    const int64_t plain = cnt_ge(g.cntU_ge, alpha) + cnt_ge(g.cntV_ge, beta);
+    return unc <= plain;
+}
+
+int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
+                 bool sync_and_check, bool pruned) {
+    // pruned (Algorithm 2, GCC+): the core-ordered graph; with dl = min(alpha, beta) and
+    // dq = max(alpha, beta), vertices with core < dl cannot be members (Lemma 1(1)) and those
+    // with core >= dq are members (Lemma 1(2)); only core in [dl, dq) is peeled, counting
+    // neighbours with core >= dl, and only those vertices are ever decremented.
+    const Graph &g = pruned ? ctx->pr.gc : ctx->g;
     PeelWork &w = ctx->w;
     ABC_TRY(peel_prepare(ctx));
     const int32_t nU = g.nU, nV = g.nV;
     const int64_t n = g.n();
-    const int32_t pU = (int32_t)cnt_ge(g.cntU_ge, alpha);
-    const int32_t pV = (int32_t)cnt_ge(g.cntV_ge, beta);
-    const int64_t P = (int64_t)pU + pV;
-    const int mode = pick_mode(ctx, alpha, beta, pU, pV);
+    const int32_t dl = std::min(alpha, beta), dq = std::max(alpha, beta);
+    const int32_t pU = (int32_t)(pruned ? cnt_ge(ctx->pr.coreU_ge, dl) : cnt_ge(g.cntU_ge, alpha));
+    const int32_t pV = (int32_t)(pruned ? cnt_ge(ctx->pr.coreV_ge, dl) : cnt_ge(g.cntV_ge, beta));
+    const int32_t cU = pruned ? (int32_t)cnt_ge(ctx->pr.coreU_ge, dq) : 0;
+    const int32_t cV = pruned ? (int32_t)cnt_ge(ctx->pr.coreV_ge, dq) : 0;
+    const int64_t P = (int64_t)pU + pV, Pu = (int64_t)(pU - cU) + (pV - cV);
+    const int mode = pruned ? 3 : pick_mode(ctx, alpha, beta, pU, pV);
 
     const int slot = w.next;
     if (w.pending[slot]) ABC_TRY(peel_finish(ctx));  // ring wrapped: wait for the oldest peels
@@ -248,6 +271,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.nV = nV;
     a.pU = pU;
     a.pV = pV;
+    a.cU = cU;
+    a.cV = cV;
     a.thrU = alpha;
     a.thrV = beta;
     a.chunk = std::max(ctx->prm.chunk, 32);
@@ -255,8 +280,9 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
     a.searchU = mode & 1;
     a.searchV = (mode >> 1) & 1;
-    a.hubcutU = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, ctx->prm.hub_degree), pU) : 0;
-    a.hubcutV = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), pV) : 0;
+    const bool hubs = ctx->prm.hub_degree > 0 && !pruned;
+    a.hubcutU = hubs ? (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, ctx->prm.hub_degree), pU) : 0;
+    a.hubcutV = hubs ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), pV) : 0;
     a.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
     a.old2new = g.old2new;
     a.new2old = g.new2old;
@@ -274,7 +300,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
 
     SlotInfo &si = w.info[slot];
     si = SlotInfo{};
-    si.cands = P;
+    si.cands = pruned ? Pu : P;
     si.n = n;
     si.emit = a.emit;
     si.timed = ctx->prm.timing != 0;
@@ -291,8 +317,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
     }
     if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
-    if (P > 0) {
-        const int64_t gi = std::min<int64_t>((P + INIT_THREADS - 1) / INIT_THREADS, (int64_t)ctx->num_sms * 32);
+    if (Pu > 0) {
+        const int64_t gi = std::min<int64_t>((Pu + INIT_THREADS - 1) / INIT_THREADS, (int64_t)ctx->num_sms * 32);
         k_init<<<(unsigned)std::max<int64_t>(gi, 1), INIT_THREADS, 0, ctx->stream>>>(a);
         si.has_init = true;
         ctx->stats.launches++;

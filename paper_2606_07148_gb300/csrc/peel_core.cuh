@@ -59,10 +59,10 @@ __device__ __forceinline__ bool stream_skips(const PeelArgs &a, int32_t y, bool 
 __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper_row, int32_t &thr) {
     if (upper_row) {
         thr = a.thrV;
-        return y < a.nU + a.pV;
+        return y < a.nU + a.pV && y >= a.nU + a.cV;
     }
     thr = a.thrU;
-    return y < a.pU;
+    return y < a.pU && y >= a.cU;
 }
 
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in
@@ -110,6 +110,11 @@ __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, in
     if (want && fallen) {
         ls.pushes++;
         if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+        if (a.corev) a.corev[y] = a.step;
+    }
+    if (a.removed) {
+        const unsigned fm = __ballot_sync(ABC_FULL, want && fallen);
+        if (fm && (threadIdx.x & 31) == 0) atomicAdd(a.removed, (unsigned long long)__popc(fm));
     }
     const bool keep = want && nch > 0;
     const unsigned pm = __ballot_sync(ABC_FULL, keep);
@@ -348,6 +353,55 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
     }
 }
 
+// Bounded barrier over the `G` blocks of one group (a batch chain, or a whole launch). The last block to arrive can run `fixup`
+// while every other block of the group waits. Returns false if the group saw an error.
+//
+// With `watch`, the last block to arrive also records whether *watch has reached `limit` in
+// bar[16], which every block can read once the barrier has passed (it changes only at the next
+// such barrier, so all blocks read the same value).
+__device__ __forceinline__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl, bool fixup, unsigned long long timeout_ns,
+                                              const unsigned long long *watch = nullptr,
+                                              unsigned long long limit = 0) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *genp = bar + 32;
+        const unsigned gen = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == (unsigned)G - 1) {
+            atomicExch(bar, 0u);
+            if (watch) bar[16] = ld_relaxed(watch) >= limit ? 1u : 0u;
+            if (fixup) {
+                // the cascade closed the queue: the tickets it voided, [tail, old head), were
+                // emptied by their holders, so the next step's tickets restart at tail
+                const unsigned long long t = ld_relaxed(&ctl->tail);
+                atomicExch(&ctl->head, t);
+                atomicExch(&ctl->done, t);
+            }
+            __threadfence();
+            atomicAdd(bar + 32, 1u);
+        } else {
+            const unsigned long long t0 = now_ns();
+            unsigned sl = 32;
+            while (*genp == gen) {
+                if (now_ns() - t0 > timeout_ns) {
+                    set_error(&ctl->err, ABCORE_ETIMEDOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(sl);
+                if (sl < 512) sl <<= 1;
+            }
+        }
+        __threadfence();
+        if (ld_relaxed_i32(&ctl->err) != 0) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // Candidate counts (the scan phase): thread t of nthreads handles candidates t, t + nthreads, ...
 // Per layer, the count is either the row prefix below the other layer's candidate boundary
 // (binary search in the sorted row) or the full degree (to be corrected by stream_range).
@@ -355,7 +409,7 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
 template <int CAP>
 __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, int64_t t0, int64_t nthreads,
                                            LaneStats &ls, unsigned long long &probes, unsigned long long &inits) {
-    const int64_t P = (int64_t)a.pU + a.pV;
+    const int64_t nu = (int64_t)a.pU - a.cU, P = nu + (a.pV - a.cV);  // uncertain candidates
     const int lane = threadIdx.x & 31;
     int pc = 0;
     for (int64_t b = t0 - lane; b < P; b += nthreads) {
@@ -364,7 +418,7 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
         int32_t x = 0;
         int nch = 0;
         if (i < P) {
-            x = i < a.pU ? (int32_t)i : (int32_t)(a.nU + (i - a.pU));
+            x = i < nu ? (int32_t)(a.cU + i) : (int32_t)(a.nU + a.cV + (i - nu));
             const bool upper = x < a.nU;
             const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
             int len;
@@ -469,8 +523,8 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                                            LaneStats &ls, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
     int pc = 0;
-    const int64_t u0 = a.searchU ? a.pU : a.hubcutU;  // U ids [u0, pU) counted by degree
-    const int64_t v0 = a.searchV ? a.pV : a.hubcutV;  // V ids nU + [v0, pV)
+    const int64_t u0 = a.searchU ? a.pU : max(a.hubcutU, a.cU);  // U ids [u0, pU) counted by degree
+    const int64_t v0 = a.searchV ? a.pV : max(a.hubcutV, a.cV);  // V ids nU + [v0, pV)
     const int64_t nu = a.pU - u0, total = nu + (a.pV - v0);
     for (int64_t b = t0 - lane; b < total; b += nthreads) {
         const int64_t i = b + lane;

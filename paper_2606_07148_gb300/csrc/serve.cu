@@ -780,7 +780,8 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
     s->alphas.assign(ta, ta + nt);
     s->betas.assign(tb, tb + nt);
     s->slots = slots;
-    s->dcap = 2 * (int64_t)std::max<int32_t>(slots, 1 << 16) + 1024;
+    // inserted-edge pool per target: two list nodes (16 bytes each) per inserted edge
+    s->dcap = 2 * std::max<int64_t>(slots, ctx->prm.serve_inserts) + 1024;
     ABC_CU(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     ABC_CU(cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming));
     ABC_CU(cudaHostAlloc(&s->h_req, sizeof(abcore_req) * slots, cudaHostAllocMapped));
