@@ -240,13 +240,19 @@ def run_peel(args, rank, world, local):
     m = spec["m"]
     pairs = peel_pairs_for(name, spec)
     core = ABCore(local)
-    apply_params(core, args)
+    core.set_param("algo", 1)  # the headline is the plain (index-free) peel; GCC+ is reported apart
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     core.load_edges(nU, nV, eu, ev)
     e1.record()
     torch.cuda.synchronize()
     csr_ms = e0.elapsed_time(e1)
+    tuned, tune_s = None, 0.0
+    if not args.no_autotune:
+        t = time.perf_counter()
+        _, tuned = core.autotune(pairs)
+        tune_s = time.perf_counter() - t
+    apply_params(core, args)
     eu_h = eu.cpu().numpy() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     ev_h = ev.cpu().numpy() if eu_h is not None else None
     del eu, ev
@@ -323,6 +329,38 @@ def run_peel(args, rank, world, local):
     e2e = {"value": round(world * len(pairs) * m / e2e_s / 1e9, 3), "unit": "GTEPS",
            "h2d_bytes_per_step": 8 * len(pairs), "d2h_bytes_per_step": len(pairs) * (nU + nV)}
 
+    # Algorithm 2 (GCC+): one-time core decomposition and core-ordered layout, then the same
+    # queries pruned by Lemma 1 (each query takes whichever of GCC / GCC+ leaves fewer vertices)
+    gccp = None
+    if not args.no_gccplus:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, _, maxcore = core.core_numbers()
+        torch.cuda.synchronize()
+        prep_ms = (time.perf_counter() - t) * 1e3
+        core.set_param("algo", 0)
+        ref = [(ou.clone(), ov.clone()) for ou, ov in outs]
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        core.sync()
+        pevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            pevs[i][0].record()
+            step()
+            pevs[i][1].record()
+        core.sync()
+        torch.cuda.synchronize()
+        pms = allreduce_max(statistics.mean([a.elapsed_time(b) for a, b in pevs]), world, dev)
+        same = all(torch.equal(r[0], o[0]) and torch.equal(r[1], o[1]) for r, o in zip(ref, outs))
+        gccp = {"preprocess_ms": round(prep_ms, 2), "max_core": maxcore, "ms_per_step": round(pms, 4),
+                "value": round(world * len(pairs) * m / (pms / 1e3) / 1e9, 3), "unit": "GTEPS",
+                "masks_identical_to_plain": same,
+                "note": "per query the pruned peel runs when it leaves fewer vertices than the plain one; "
+                        "preprocessing (core decomposition + core-ordered CSR) is excluded from ms_per_step"}
+        core.set_param("algo", 1)
+
     cpu = None
     parity = None
     if eu_h is not None:
@@ -343,9 +381,10 @@ def run_peel(args, rank, world, local):
                    "csr_build_ms": round(csr_ms, 2), "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write); CSR %.2f GB > 129 MB L2"
                          % ((8 * (nU + nV + 1) + 8 * m) / 1e9),
-                   "timed_wall_s": round(t_wall, 4)},
+                   "timed_wall_s": round(t_wall, 4), "algorithm": "GCC (plain peel, Algorithm 1)",
+                   "autotuned": tuned, "autotune_s": round(tune_s, 2), "params": args.param},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "cpu_baseline": cpu, "parity": parity,
+        "cpu_baseline": cpu, "parity": parity, "gccplus": gccp,
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4)},
     }
     core.close()
@@ -368,7 +407,6 @@ def run_batch(args, rank, world, local):
     if base.startswith("billion"):
         pairs = pairs[1:]  # the 8 x 8 grid; the single (64, 64) core is the peel workload
     core = ABCore(local)
-    apply_params(core, args)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     core.load_edges(nU, nV, eu, ev)
@@ -377,6 +415,12 @@ def run_batch(args, rank, world, local):
     csr_ms = e0.elapsed_time(e1)
     del eu, ev
     torch.cuda.empty_cache()
+    tuned, tune_s = None, 0.0
+    if not args.no_autotune:
+        t = time.perf_counter()
+        _, tuned = core.autotune(pairs, batch=True)
+        tune_s = time.perf_counter() - t
+    apply_params(core, args)
     a = [p[0] for p in pairs]
     b = [p[1] for p in pairs]
     mu = torch.empty((len(pairs), nU), dtype=torch.uint8, device=dev)
@@ -455,7 +499,7 @@ def run_batch(args, rank, world, local):
                    "grid": sorted(set(a)), "csr_build_ms": round(csr_ms, 2),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write)", "timed_wall_s": round(t_wall, 3),
-                   "params": args.param},
+                   "params": args.param, "autotuned": tuned, "autotune_s": round(tune_s, 2)},
         "clocks": clk,
         "e2e": {"value": round(world * len(pairs) / e2e_s, 2), "unit": "cores/s", "h2d_bytes_per_step": 8 * len(pairs),
                 "d2h_bytes_per_step": len(pairs) * (nU + nV)},
@@ -531,6 +575,21 @@ def run_serve(args, rank, world, local):
         core.close()
     clk = clocks.stop()
     same = all(answers[r] == answers[spec["rates"][0]] for r in spec["rates"])
+    # component labels (the GFQ preprocessing) on the base graph, timed on the device
+    core = ABCore(local)
+    core.load_edges(nU, nV, eu, ev)
+    lu = torch.empty(nU, dtype=torch.int32, device=dev)
+    lv = torch.empty(nV, dtype=torch.int32, device=dev)
+    core.components(lu, lv)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    _, _, ncomp = core.components(lu, lv)
+    c1.record()
+    torch.cuda.synchronize()
+    largest = int(torch.bincount(torch.cat([lu, lv]).long()).max().item())
+    comps = {"ms": round(c0.elapsed_time(c1), 3), "components": ncomp, "largest": largest,
+             "vertices": nU + nV}
+    core.close()
     # comparator on the same GPU: one full plain peel of the graph per query
     core = ABCore(local)
     core.load_edges(nU, nV, eu, ev)
@@ -556,7 +615,7 @@ def run_serve(args, rank, world, local):
         "config": {"workload": args.workload, "graph": describe(spec, args.workload), "updates": n_ops,
                    "targets": [list(t) for t in targets], "stream_gen_s": round(gen_s, 2),
                    "parallelism": "single"},
-        "rates": results, "answers_identical_across_rates": same,
+        "rates": results, "answers_identical_across_rates": same, "components": comps,
         "plain_full_peel_per_query_qps": round(plain_qps, 1), "clocks": clk,
         "e2e": {"value": top["p99_ms"], "unit": "ms", "h2d_bytes_per_step": n_ops * req_size,
                 "d2h_bytes_per_step": n_ops * ctypes_sizeof(abi.abcore_resp)},
@@ -625,6 +684,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="peel-4Mx2M-80M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--no-gccplus", action="store_true", help="skip the GCC+ (core-number pruned) leg")
     ap.add_argument("--serve-ops", type=int, default=0, help="updates per rate (default: the workload's)")
     ap.add_argument("--param", action="append", default=[], help="library parameter name=value (repeatable)")
     args = ap.parse_args()

@@ -151,6 +151,25 @@ int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32
 int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
                          uint8_t *masks_u, uint8_t *masks_v, uint32_t flags);
 
+/* ---- autotuning ---------------------------------------------------------------------------- */
+
+#define ABCORE_TUNE_PEEL  0u  /* tune abcore_compute on the sample, one call per pair           */
+#define ABCORE_TUNE_BATCH 1u  /* tune abcore_compute_batch on the sample, one batch of n pairs  */
+
+/* Pick the launch and cascade parameters by measurement on the loaded graph: blocks per SM,
+ * adjacency entries per work item ("chunk"), the queue's grab divisor, the hub degree above
+ * which counts always come from a row search, the probe cost that steers the per-layer choice
+ * between searching candidate rows and streaming violator rows, the scatter-versus-gather
+ * switch of the mask emission, and for batches the number of chains sharing the GPU. Coordinate
+ * descent; every setting is timed with CUDA events on the context's stream, best of three runs
+ * of the whole sample with L2 flushed before each. The fastest setting stays on the context
+ * (abcore_set_param changes it again); *best_ms (may be NULL) receives its sample time. Results
+ * never depend on these parameters. Takes a few hundred timed runs of the sample.
+ * Errors: EINVAL (empty sample, negative threshold, more than 64 pairs for ABCORE_TUNE_PEEL),
+ * ENOTLOADED, ENOMEM, ETIMEDOUT. */
+int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
+                    uint32_t what, double *best_ms);
+
 /* Wait for work enqueued with ABCORE_ASYNC and return its status. */
 int abcore_sync(abcore_ctx *ctx);
 
@@ -223,6 +242,10 @@ int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
 
 /* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown. */
 int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
+
+/* Current value of a tuning parameter (the names abcore_set_param takes, except the actions
+ * "reset_stats" and "debug_stall_slots"); EINVAL if unknown. */
+int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value);
 
 /* Graph sizes of the loaded graph; any pointer may be NULL. */
 int abcore_graph_info(abcore_ctx *ctx, int32_t *nU, int32_t *nV, int64_t *m,

@@ -134,6 +134,17 @@ class ABCore:
                                              b.ctypes.data_as(ctypes.c_void_p), pu, pv, fl))
         return out_u, out_v
 
+    def autotune(self, pairs, batch=False):
+        """Tune the launch parameters on a sample of (alpha, beta) pairs; returns the best sample
+        time in ms and the chosen parameters."""
+        a = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+        b = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+        best = ctypes.c_double(0)
+        what = abi.ABCORE_TUNE_BATCH if batch else abi.ABCORE_TUNE_PEEL
+        self._check(abi.abcore_autotune(self._h, len(pairs), a.ctypes.data_as(ctypes.c_void_p),
+                                        b.ctypes.data_as(ctypes.c_void_p), what, ctypes.byref(best)))
+        return best.value, {k: self.get_param(k) for k in self.TUNED}
+
     def sync(self):
         self._check(abi.abcore_sync(self._h))
 
@@ -201,6 +212,14 @@ class ABCore:
 
     def set_param(self, name, value):
         self._check(abi.abcore_set_param(self._h, name.encode(), int(value)))
+
+    def get_param(self, name):
+        v = ctypes.c_int64(0)
+        self._check(abi.abcore_get_param(self._h, name.encode(), ctypes.byref(v)))
+        return int(v.value)
+
+    TUNED = ("blocks_per_sm", "chunk", "grab_div", "hub_degree", "probe_bytes", "emit_scatter_max_pct",
+             "batch_wave")
 
     def graph_info(self):
         nU, nV, du, dv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -19,6 +19,8 @@ ABCORE_ECUDA = -6
 ABCORE_ETIMEDOUT = -7
 ABCORE_EBUSY = -8
 
+ABCORE_TUNE_PEEL = 0
+ABCORE_TUNE_BATCH = 1
 ABCORE_PTR_HOST = 0
 ABCORE_PTR_DEVICE = 1
 ABCORE_VALIDATE = 2
@@ -29,9 +31,9 @@ ABCORE_DELETE = 1
 
 EXPORTED = [
     "abcore_create", "abcore_destroy", "abcore_last_error", "abcore_load_edges", "abcore_load_csr",
-    "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_core_numbers", "abcore_query_edge",
+    "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_core_numbers", "abcore_autotune", "abcore_query_edge",
     "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
-    "abcore_get_stats", "abcore_set_param", "abcore_graph_info", "abcore_export_csr",
+    "abcore_get_stats", "abcore_set_param", "abcore_get_param", "abcore_graph_info", "abcore_export_csr",
     "abcore_compute_static",
 ]
 
@@ -96,6 +98,8 @@ def load_library(path: str = LIB):
         "abcore_compute": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
         "abcore_compute_batch": ([_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
         "abcore_sync": ([_vp], ctypes.c_int),
+        "abcore_autotune": ([_vp, ctypes.c_int32, _vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
         "abcore_core_numbers": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32], ctypes.c_int),
         "abcore_components": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32], ctypes.c_int),
         "abcore_query_edge": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
@@ -106,6 +110,7 @@ def load_library(path: str = LIB):
         "abcore_serve_stop": ([_vp], ctypes.c_int),
         "abcore_get_stats": ([_vp, ctypes.POINTER(abcore_stats)], ctypes.c_int),
         "abcore_set_param": ([_vp, ctypes.c_char_p, ctypes.c_int64], ctypes.c_int),
+        "abcore_get_param": ([_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "abcore_graph_info": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "abcore_export_csr": ([_vp, _vp, _vp, _vp, ctypes.c_uint32], ctypes.c_int),
         "abcore_compute_static": ([ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
@@ -136,6 +141,7 @@ abcore_compute_batch = _fn("abcore_compute_batch")
 abcore_sync = _fn("abcore_sync")
 abcore_components = _fn("abcore_components")
 abcore_core_numbers = _fn("abcore_core_numbers")
+abcore_autotune = _fn("abcore_autotune")
 abcore_query_edge = _fn("abcore_query_edge")
 abcore_serve_start = _fn("abcore_serve_start")
 abcore_serve_submit = _fn("abcore_serve_submit")
@@ -143,6 +149,7 @@ abcore_serve_poll = _fn("abcore_serve_poll")
 abcore_serve_stop = _fn("abcore_serve_stop")
 abcore_get_stats = _fn("abcore_get_stats")
 abcore_set_param = _fn("abcore_set_param")
+abcore_get_param = _fn("abcore_get_param")
 abcore_graph_info = _fn("abcore_graph_info")
 abcore_export_csr = _fn("abcore_export_csr")
 abcore_compute_static = _fn("abcore_compute_static")

@@ -280,6 +280,26 @@ int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64
     return rc;
 }
 
+int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint32_t what,
+                    double *best_ms) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    if (n <= 0 || !alphas || !betas) return ctx->fail(ABCORE_EINVAL, "autotune needs at least one (alpha, beta)");
+    if (what & ~ABCORE_TUNE_BATCH) return ctx->fail(ABCORE_EINVAL, "unknown autotune target");
+    if (!(what & ABCORE_TUNE_BATCH) && n > CTL_RING) return ctx->fail(ABCORE_EINVAL, "at most %d queries per sample", CTL_RING);
+    for (int32_t i = 0; i < n; ++i)
+        if (alphas[i] < 0 || betas[i] < 0) return ctx->fail(ABCORE_EINVAL, "alpha and beta must be >= 0");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(peel_finish(ctx));
+    if (ctx->g.n() == 0) {
+        if (best_ms) *best_ms = 0;
+        return ABCORE_OK;
+    }
+    return autotune(ctx, n, alphas, betas, what, best_ms);
+}
+
 int abcore_sync(abcore_ctx *ctx) {
     if (!ctx) return ABCORE_EINVAL;
     ABC_CU(cudaSetDevice(ctx->device));
@@ -404,6 +424,26 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
     } else {
         return ctx->fail(ABCORE_EINVAL, "unknown parameter '%s'", name);
     }
+    return ABCORE_OK;
+}
+
+int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
+    if (!ctx || !name || !value) return ABCORE_EINVAL;
+    const Params &p = ctx->prm;
+    const std::string k(name);
+    if (k == "chunk") *value = p.chunk;
+    else if (k == "grab_div") *value = p.grab_div;
+    else if (k == "blocks_per_sm") *value = p.blocks_per_sm;
+    else if (k == "mode") *value = p.mode;
+    else if (k == "timeout_ms") *value = p.timeout_ms;
+    else if (k == "emit_scatter_max_pct") *value = p.emit_scatter_max_pct;
+    else if (k == "probe_bytes") *value = (int64_t)p.probe_bytes;
+    else if (k == "batch_wave") *value = p.batch_wave;
+    else if (k == "hub_degree") *value = p.hub_degree;
+    else if (k == "timing") *value = p.timing;
+    else if (k == "serve_inserts") *value = p.serve_inserts;
+    else if (k == "algo") *value = p.algo;
+    else return ctx->fail(ABCORE_EINVAL, "unknown parameter '%s'", name);
     return ABCORE_OK;
 }
 

@@ -251,6 +251,10 @@ int build_graph(abcore_ctx *ctx, Graph &g, int32_t nU, int32_t nV, int64_t m, co
                 const int32_t *d_ev, const int32_t *d_rank, int32_t maxrank);
 int csr_edges(abcore_ctx *ctx, const Graph &g, int32_t *d_eu, int32_t *d_ev);  // caller-id edge list
 
+// tune.cu -- autotuner
+int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint32_t what,
+             double *best_ms);
+
 // coredecomp.cu -- core numbers and the GCC+ layout
 int prepare_pruning(abcore_ctx *ctx);
 void free_pruning(abcore_ctx *ctx);

@@ -235,3 +235,27 @@ def test_peel_full_size_4Mx2M_80M():
     off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
     _check_pairs(core, nU, nV, eu, ev, spec["pairs"], off, adj)
     core.close()
+
+
+def test_autotune_keeps_results_exact():
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    pairs = [(2, 3), (3, 2), (5, 5), (8, 2)]
+    best, chosen = core.autotune(pairs)
+    assert best > 0
+    assert chosen["blocks_per_sm"] in (0, 2, 3) and chosen["chunk"] in (256, 512, 1024, 2048)
+    assert chosen["hub_degree"] in (0, 64, 256, 1024) and chosen["probe_bytes"] in (16, 32, 64)
+    for a, b in pairs + [(1, 7), (4, 4)]:
+        mu, mv = core.compute(a, b)
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv)
+    best_b, chosen_b = core.autotune(synth.grid_pairs(4, 1, 8), batch=True)
+    assert best_b > 0 and chosen_b["batch_wave"] in (2, 4, 8, 16)
+    grid = synth.grid_pairs(4, 1, 8)
+    bu, bv = core.compute_batch([p[0] for p in grid], [p[1] for p in grid])
+    for i, (a, b) in enumerate(grid):
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        assert np.array_equal(bu[i].cpu().numpy(), wu) and np.array_equal(bv[i].cpu().numpy(), wv)
+    core.close()
