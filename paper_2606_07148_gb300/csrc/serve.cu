@@ -52,23 +52,19 @@ namespace {
 constexpr int SERVE_THREADS = 256;
 constexpr int SERVE_WARPS = SERVE_THREADS / 32;
 
-struct DNode {
-    int32_t y;      // neighbour (internal id)
-    int32_t next;   // next node of this vertex's list, -1 = end
-    int32_t alive;  // 0 once the edge is deleted again
-    int32_t pad;
-};
-
 struct TargetDev {
     int32_t alpha, beta;
     uint8_t *M;        // [n] core membership
     int32_t *cnt;      // [n] members: in-core degree; region vertices: region count
     int32_t *deg;      // [n] degree in the current graph
     uint32_t *tomb;    // [ceil(2m / 32)] deleted base adjacency slots
-    int32_t *dhead;    // [n] inserted-neighbour list heads (-1 = none)
-    DNode *dpool;      // [dcap]
-    int32_t *dcount;   // nodes used
-    int32_t dcap;
+    // inserted neighbours: vertex x owns the pool segment [ins[x].x, ins[x].x + capacity) and
+    // uses its first ins[x].y slots (-1 = none yet); a deleted one is overwritten with -1. A full
+    // segment is copied into a new one of twice the capacity (2, 4, 8, ...).
+    int2 *ins;         // [n] {segment start, entries used}
+    int32_t *pool;     // [pool_cap]
+    int32_t *pool_top; // pool entries handed out
+    int32_t pool_cap;
     int32_t *mark;     // [n] epoch tags for region / cascade membership
     int32_t *q;        // [2n] scratch queue (a region, then the region vertices it peels)
     int32_t *epoch;    // persisted epoch counter
@@ -159,19 +155,76 @@ __device__ __forceinline__ int32_t thr_of(const ServeArgs &A, const TargetDev &S
     return z < A.nU ? S.alpha : S.beta;
 }
 
+// Capacity of an inserted-neighbour segment holding `used` entries.
+__device__ __forceinline__ int32_t ins_capacity(int32_t used) {
+    int32_t c = 2;
+    while (c < used) c <<= 1;
+    return c;
+}
+
 // Visit the current neighbours of w: base row minus tombstones, plus live inserted neighbours.
-// Warp-collective: lanes stride the base row; the inserted list is walked by every lane in step.
+// Warp-collective: lanes stride the base row, then the inserted segment.
 template <class F>
 __device__ __forceinline__ void for_neighbours(const ServeArgs &A, const TargetDev &S, int32_t w, F f) {
     const int lane = threadIdx.x & 31;
     const int64_t s = __ldg(&A.off[w]), e = __ldg(&A.off[w + 1]);
     for (int64_t p = s + lane; p < e; p += 32)
         if (!tomb_get(S.tomb, p)) f(__ldg(&A.adj[p]));
-    for (int32_t nd = S.dhead[w]; nd >= 0;) {
-        const DNode d = S.dpool[nd];
-        if (lane == 0 && d.alive) f(d.y);
-        nd = d.next;
+    const int2 seg = S.ins[w];
+    for (int32_t i = lane; i < seg.y; i += 32) {
+        const int32_t z = S.pool[seg.x + i];
+        if (z >= 0) f(z);
     }
+}
+
+// Block-collective: position in the pool of inserted neighbour `key` of x, or -1.
+__device__ int32_t ins_find(const TargetDev &S, int32_t x, int32_t key) {
+    __shared__ int32_t found_s;
+    if (threadIdx.x == 0) found_s = -1;
+    __syncthreads();
+    const int2 seg = S.ins[x];
+    for (int32_t i = threadIdx.x; i < seg.y; i += SERVE_THREADS)
+        if (S.pool[seg.x + i] == key) found_s = seg.x + i;  // live entries are distinct
+    __syncthreads();
+    const int32_t r = found_s;
+    __syncthreads();
+    return r;
+}
+
+// Block-collective: append y to x's inserted neighbours, moving the segment to one of twice the
+// capacity when it is full. Returns false (and records ABCORE_ENOMEM) if the pool is exhausted.
+__device__ bool ins_append(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y) {
+    __shared__ int32_t from_s, to_s;
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        const int2 seg = S.ins[x];
+        ok_s = 1;
+        from_s = -1;
+        to_s = seg.x;
+        if (seg.x < 0 || seg.y == ins_capacity(seg.y)) {
+            const int32_t cap = seg.x < 0 ? 2 : 2 * ins_capacity(seg.y);
+            const int32_t at = atomicAdd(S.pool_top, cap);
+            if (at > S.pool_cap - cap) {
+                abc::set_error(A.err, ABCORE_ENOMEM);
+                ok_s = 0;
+            } else {
+                from_s = seg.x;
+                to_s = at;
+            }
+        }
+    }
+    __syncthreads();
+    const int2 seg = S.ins[x];
+    if (ok_s && from_s >= 0)
+        for (int32_t i = threadIdx.x; i < seg.y; i += SERVE_THREADS) S.pool[to_s + i] = S.pool[from_s + i];
+    __syncthreads();
+    if (threadIdx.x == 0 && ok_s) {
+        S.pool[to_s + seg.y] = y;
+        S.ins[x] = make_int2(to_s, seg.y + 1);
+    }
+    const bool ok = ok_s != 0;
+    __syncthreads();
+    return ok;
 }
 
 // Process queue entries level by level: each warp takes entries of the current level,
@@ -339,68 +392,53 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
 __device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t x, int32_t y, int32_t ep,
                               int *bits) {
     __shared__ int status_s;
-    __shared__ int32_t dnode_s;
     const int64_t px = cta_find(A.adj, __ldg(&A.off[x]), __ldg(&A.off[x + 1]), y);
     int64_t py = -1;
+    int32_t qx = -1;  // pool position of y among x's inserted neighbours
     if (px >= 0) py = cta_find(A.adj, __ldg(&A.off[y]), __ldg(&A.off[y + 1]), x);
-    if (threadIdx.x == 0) {
-        dnode_s = -1;
-        bool present;
-        if (px >= 0) {
-            present = !tomb_get(S.tomb, px);
-        } else {
-            present = false;
-            for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next)
-                if (S.dpool[nd].y == y && S.dpool[nd].alive) {
-                    present = true;
-                    dnode_s = nd;
-                    break;
-                }
-        }
-        int st = ABCORE_OK;
-        if (op == ABCORE_INSERT && present) st = ABCORE_EEXIST;
-        if (op == ABCORE_DELETE && !present) st = ABCORE_ENOENT;
-        status_s = st;
-        if (st == ABCORE_OK) {
-            if (op == ABCORE_INSERT) {
-                if (px >= 0) {
+    else qx = ins_find(S, x, y);
+    __shared__ int present_s;  // read once, before anything below writes the view
+    if (threadIdx.x == 0) present_s = px >= 0 ? !tomb_get(S.tomb, px) : qx >= 0;
+    __syncthreads();
+    const bool present = present_s != 0;
+    int st = ABCORE_OK;
+    if (op == ABCORE_INSERT && present) st = ABCORE_EEXIST;
+    if (op == ABCORE_DELETE && !present) st = ABCORE_ENOENT;
+    if (st == ABCORE_OK) {
+        if (op == ABCORE_INSERT) {
+            if (px >= 0) {
+                if (threadIdx.x == 0) {
                     tomb_set(S.tomb, px, false);
                     tomb_set(S.tomb, py, false);
-                } else {
-                    const int32_t a = atomicAdd(S.dcount, 2);
-                    if (a + 2 > S.dcap) {
-                        abc::set_error(A.err, ABCORE_ENOMEM);
-                        status_s = ABCORE_ENOMEM;
-                    } else {
-                        S.dpool[a] = DNode{y, S.dhead[x], 1, 0};
-                        S.dhead[x] = a;
-                        S.dpool[a + 1] = DNode{x, S.dhead[y], 1, 0};
-                        S.dhead[y] = a + 1;
-                    }
                 }
-                if (status_s == ABCORE_OK) {
-                    S.deg[x]++;
-                    S.deg[y]++;
-                }
-            } else {
-                if (px >= 0) {
+            } else if (!ins_append(A, S, x, y) || !ins_append(A, S, y, x)) {
+                st = ABCORE_ENOMEM;  // the loop stops: the pool error ends every block
+            }
+            if (threadIdx.x == 0 && st == ABCORE_OK) {
+                S.deg[x]++;
+                S.deg[y]++;
+            }
+        } else {
+            if (px >= 0) {
+                if (threadIdx.x == 0) {
                     tomb_set(S.tomb, px, true);
                     tomb_set(S.tomb, py, true);
-                } else {
-                    S.dpool[dnode_s].alive = 0;
-                    for (int32_t nd = S.dhead[y]; nd >= 0; nd = S.dpool[nd].next)
-                        if (S.dpool[nd].y == x && S.dpool[nd].alive) {
-                            S.dpool[nd].alive = 0;
-                            break;
-                        }
                 }
+            } else {
+                const int32_t qy = ins_find(S, y, x);
+                if (threadIdx.x == 0) {
+                    S.pool[qx] = -1;
+                    S.pool[qy] = -1;
+                }
+            }
+            if (threadIdx.x == 0) {
                 S.deg[x]--;
                 S.deg[y]--;
             }
         }
     }
+    if (threadIdx.x == 0) status_s = st;
     __syncthreads();
-    const int st = status_s;
     if (st == ABCORE_OK) {
         const bool mx = S.M[x], my = S.M[y];
         __syncthreads();
@@ -513,7 +551,7 @@ __global__ void k_lv_init(const int64_t *off, int32_t nU, int32_t nV, TargetDev 
         const int32_t thr = x < nU ? S.alpha : S.beta;
         S.cnt[x] = d;
         S.deg[x] = d;
-        S.dhead[x] = -1;
+        S.ins[x] = make_int2(-1, 0);
         S.mark[x] = 0;
         if (d < thr) {
             S.rho[x] = 0;
@@ -564,12 +602,13 @@ __global__ void k_collect_edges(const int64_t *off, const int32_t *adj, const in
         ev[i] = new2old[adj[p]];
     }
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nU; x += (int64_t)gridDim.x * blockDim.x) {
-        for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next) {
-            const DNode d = S.dpool[nd];
-            if (!d.alive) continue;
-            const unsigned long long i = atomicAdd(count, 1ull);
-            eu[i] = new2old[x];
-            ev[i] = new2old[d.y];
+        const int2 seg = S.ins[x];
+        for (int32_t i = 0; i < seg.y; ++i) {
+            const int32_t z = S.pool[seg.x + i];
+            if (z < 0) continue;
+            const unsigned long long k = atomicAdd(count, 1ull);
+            eu[k] = new2old[x];
+            ev[k] = new2old[z];
         }
     }
 }
@@ -577,9 +616,10 @@ __global__ void k_collect_edges(const int64_t *off, const int32_t *adj, const in
 // Union the inserted edges of the current graph (view of target 0) into a component forest.
 __global__ void k_cc_inserted(int32_t nU, TargetDev S, int32_t *parent) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nU; x += (int64_t)gridDim.x * blockDim.x) {
-        for (int32_t nd = S.dhead[x]; nd >= 0; nd = S.dpool[nd].next) {
-            const DNode d = S.dpool[nd];
-            if (d.alive) abc::cc_unite(parent, (int32_t)x, d.y);
+        const int2 seg = S.ins[x];
+        for (int32_t i = 0; i < seg.y; ++i) {
+            const int32_t z = S.pool[seg.x + i];
+            if (z >= 0) abc::cc_unite(parent, (int32_t)x, z);
         }
     }
 }
@@ -609,7 +649,7 @@ struct ServeState {
     cudaEvent_t loop_done = nullptr;
     bool loop_launched = false;
     bool dirty = false;  // updates applied since the CSR was built
-    int64_t dcap = 0;
+    int64_t pool_cap = 0;
 };
 
 static int64_t *ctl_stop_ptr(unsigned long long *ctl) { return (int64_t *)(ctl + 8); }
@@ -719,7 +759,7 @@ static int materialize(abcore_ctx *ctx) {
     ServeState *s = ctx->serve;
     if (!s || !s->dirty || s->tdev.empty()) return ABCORE_OK;
     const Graph &g = ctx->g;
-    const int64_t cap = g.m + s->dcap / 2 + 16;
+    const int64_t cap = g.m + s->pool_cap / 2 + 16;  // every inserted edge holds two pool entries
     int32_t *eu = nullptr, *ev = nullptr;
     unsigned long long *cnt = nullptr;
     ABC_TRY(ctx->alloc(&eu, (size_t)cap, "rebuild edges"));
@@ -780,8 +820,10 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
     s->alphas.assign(ta, ta + nt);
     s->betas.assign(tb, tb + nt);
     s->slots = slots;
-    // inserted-edge pool per target: two list nodes (16 bytes each) per inserted edge
-    s->dcap = 2 * std::max<int64_t>(slots, ctx->prm.serve_inserts) + 1024;
+    // inserted-neighbour pool per target: an inserted edge takes one entry in each endpoint's
+    // segment, and segments that fill up move to twice the room, so 8 entries (32 bytes) per
+    // insert cover even one insert per vertex
+    s->pool_cap = std::min<int64_t>(8 * std::max<int64_t>(slots, ctx->prm.serve_inserts) + 1024, INT32_MAX);
     ABC_CU(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     ABC_CU(cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming));
     ABC_CU(cudaHostAlloc(&s->h_req, sizeof(abcore_req) * slots, cudaHostAllocMapped));
@@ -813,9 +855,9 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
         ABC_TRY(serve_alloc(ctx, s, &T.cnt, (size_t)std::max<int64_t>(n, 1), "serve counts"));
         ABC_TRY(serve_alloc(ctx, s, &T.deg, (size_t)std::max<int64_t>(n, 1), "serve degrees"));
         ABC_TRY(serve_alloc(ctx, s, &T.tomb, (size_t)tomb_words, "serve tombstones"));
-        ABC_TRY(serve_alloc(ctx, s, &T.dhead, (size_t)std::max<int64_t>(n, 1), "serve lists"));
-        ABC_TRY(serve_alloc(ctx, s, &T.dpool, (size_t)s->dcap, "serve list pool"));
-        ABC_TRY(serve_alloc(ctx, s, &T.dcount, 1, "serve list pool"));
+        ABC_TRY(serve_alloc(ctx, s, &T.ins, (size_t)std::max<int64_t>(n, 1), "serve inserted segments"));
+        ABC_TRY(serve_alloc(ctx, s, &T.pool, (size_t)s->pool_cap, "serve inserted pool"));
+        ABC_TRY(serve_alloc(ctx, s, &T.pool_top, 1, "serve inserted pool"));
         ABC_TRY(serve_alloc(ctx, s, &T.mark, (size_t)std::max<int64_t>(n, 1), "serve marks"));
         ABC_TRY(serve_alloc(ctx, s, &T.q, (size_t)std::max<int64_t>(2 * n, 1), "serve queue"));
         ABC_TRY(serve_alloc(ctx, s, &T.epoch, 1, "serve epoch"));
@@ -823,9 +865,9 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
         ABC_TRY(serve_alloc(ctx, s, &T.base, 1, "serve certificate"));
         ABC_TRY(serve_alloc(ctx, s, &T.st, 4, "serve stats"));
         ABC_CU(cudaMemsetAsync(T.st, 0, 4 * sizeof(unsigned long long), ctx->stream));
-        T.dcap = (int32_t)s->dcap;
+        T.pool_cap = (int32_t)s->pool_cap;
         ABC_CU(cudaMemsetAsync(T.tomb, 0, sizeof(uint32_t) * tomb_words, ctx->stream));
-        ABC_CU(cudaMemsetAsync(T.dcount, 0, sizeof(int32_t), ctx->stream));
+        ABC_CU(cudaMemsetAsync(T.pool_top, 0, sizeof(int32_t), ctx->stream));
         ABC_CU(cudaMemsetAsync(T.epoch, 0, sizeof(int32_t), ctx->stream));
         // the target's core and certificate on the current graph, by a level-synchronous peel
         {
