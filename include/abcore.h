@@ -142,6 +142,22 @@ int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta,
 int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32_t *max_core,
                         uint32_t flags);
 
+/* alpha_offset of the paper's default query (Section 6): the largest beta >= 1 whose
+ * (alpha, beta)-core is non-empty, or 0 if none is. Found by binary search over beta with the
+ * peel (the core shrinks as beta grows, by the nested property). With the default query
+ * alpha = 0.4 * delta (delta = the largest core number, abcore_core_numbers' max_core) and
+ * beta = 0.6 * alpha_offset. alpha must be at least 1 (with alpha = 0 the upper layer alone is
+ * a core for every beta). Errors: EINVAL, ENOTLOADED, ETIMEDOUT. */
+int abcore_alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_offset);
+
+/* Community search (Section 5, the Remark after GFQ): the connected component of the
+ * (alpha, beta)-core that contains vertex `id` of layer `layer` (0 = U, 1 = V). mask_u[nU] and
+ * mask_v[nV] receive 1 for its members; all zero if the vertex is not in the core. *size (may
+ * be NULL) receives the member count. Errors: EINVAL (bad layer, id or threshold, NULL mask),
+ * ENOTLOADED, ENOMEM, ETIMEDOUT. */
+int abcore_community(abcore_ctx *ctx, int32_t layer, int32_t id, int32_t alpha, int32_t beta,
+                     uint8_t *mask_u, uint8_t *mask_v, int64_t *size, uint32_t flags);
+
 /* Compute n cores at once (Lemma 1 and Algorithm 2 generalised: pairs sharing alpha are peeled
  * as one chain of increasing beta, each core seeded from the one containing it). Pair i is
  * (alphas[i], betas[i]); its masks are rows i of masks_u (n x nU, row-major) and masks_v

@@ -160,6 +160,33 @@ class ABCore:
         self._check(abi.abcore_core_numbers(self._h, pu, pv, ctypes.byref(mx), fl))
         return out_u, out_v, int(mx.value)
 
+    def alpha_offset(self, alpha):
+        """Largest beta >= 1 with a non-empty (alpha, beta)-core (0 if none)."""
+        b = ctypes.c_int32(0)
+        self._check(abi.abcore_alpha_offset(self._h, int(alpha), ctypes.byref(b)))
+        return int(b.value)
+
+    def default_query(self):
+        """The paper's default query: delta = largest core number, alpha = floor(0.4 delta),
+        beta = floor(0.6 alpha_offset(alpha)). Returns (delta, alpha, alpha_offset, beta)."""
+        _, _, delta = self.core_numbers()
+        alpha = max(1, int(0.4 * delta))
+        off = self.alpha_offset(alpha)
+        return delta, alpha, off, int(0.6 * off)
+
+    def community(self, layer, vid, alpha, beta, out_u=None, out_v=None):
+        """Masks of the (alpha, beta)-core's component containing vertex vid of layer (0 U, 1 V)."""
+        torch = _torch()
+        if out_u is None:
+            out_u = torch.empty(self.nU, dtype=torch.uint8, device="cuda:%d" % self.device)
+            out_v = torch.empty(self.nV, dtype=torch.uint8, device="cuda:%d" % self.device)
+        pu, fl = self._ptr(out_u)
+        pv, _ = self._ptr(out_v)
+        size = ctypes.c_int64(0)
+        self._check(abi.abcore_community(self._h, int(layer), int(vid), int(alpha), int(beta), pu, pv,
+                                         ctypes.byref(size), fl))
+        return out_u, out_v, int(size.value)
+
     def components(self, out_u=None, out_v=None):
         """Component labels (int32, the smallest unified caller id in each component) and the
         number of components; device tensors unless outputs are given."""

@@ -280,6 +280,56 @@ int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64
     return rc;
 }
 
+int abcore_alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_offset) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    // with alpha = 0 the upper layer alone is a core for every beta: no offset exists
+    if (alpha < 1 || !beta_offset) return ctx->fail(ABCORE_EINVAL, "alpha must be >= 1 and beta_offset non-NULL");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    if (ctx->g.n() == 0) {
+        *beta_offset = 0;
+        return ABCORE_OK;
+    }
+    return alpha_offset(ctx, alpha, beta_offset);
+}
+
+int abcore_community(abcore_ctx *ctx, int32_t layer, int32_t id, int32_t alpha, int32_t beta, uint8_t *mask_u,
+                     uint8_t *mask_v, int64_t *size, uint32_t flags) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    const Graph &g = ctx->g;
+    if (alpha < 0 || beta < 0) return ctx->fail(ABCORE_EINVAL, "alpha and beta must be >= 0");
+    if (layer != 0 && layer != 1) return ctx->fail(ABCORE_EINVAL, "layer must be 0 (U) or 1 (V)");
+    if (id < 0 || id >= (layer == 0 ? g.nU : g.nV)) return ctx->fail(ABCORE_EINVAL, "vertex id out of range");
+    if ((g.nU > 0 && !mask_u) || (g.nV > 0 && !mask_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(peel_finish(ctx));
+    int32_t q = 0;
+    ABC_CU(cudaMemcpyAsync(&q, g.old2new + (layer == 0 ? 0 : g.nU) + id, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    uint8_t *du = mask_u, *dv = mask_v, *tmp = nullptr;
+    if (!ptr_on_device(flags)) {
+        ABC_TRY(ctx->alloc(&tmp, (size_t)g.n(), "community masks"));
+        du = tmp;
+        dv = tmp + g.nU;
+    }
+    int rc = community(ctx, q, alpha, beta, du, dv, size);
+    if (!rc && tmp) {
+        cudaError_t e = cudaSuccess;
+        if (g.nU) e = cudaMemcpyAsync(mask_u, du, (size_t)g.nU, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && g.nV) e = cudaMemcpyAsync(mask_v, dv, (size_t)g.nV, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = ctx->cuda_fail(e, "community mask download");
+    }
+    ctx->release(tmp);
+    return rc;
+}
+
 int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint32_t what,
                     double *best_ms) {
     if (!ctx) return ABCORE_EINVAL;

@@ -23,23 +23,30 @@ __device__ __forceinline__ bool slot_deleted(const uint32_t *tomb, int64_t p) {
     return tomb != nullptr && ((__ldg(&tomb[p >> 5]) >> (p & 31)) & 1u);
 }
 
+// An edge counts if its slot is not deleted and, with a `keep` mask, both endpoints are kept.
+__device__ __forceinline__ bool edge_kept(const uint32_t *tomb, const uint8_t *keep, int64_t p, int32_t x, int32_t y) {
+    return !slot_deleted(tomb, p) && (keep == nullptr || (__ldg(&keep[x]) && __ldg(&keep[y])));
+}
+
 __global__ void k_cc_init(int32_t *parent, int64_t n) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         parent[x] = (int32_t)x;
 }
 
 // rows [r0, r1): one block per row
-__global__ void k_cc_hook_block(const int64_t *off, const int32_t *adj, const uint32_t *tomb, int32_t *parent,
+__global__ void k_cc_hook_block(const int64_t *off, const int32_t *adj, const uint32_t *tomb, const uint8_t *keep,
+                                int32_t *parent,
                                 int32_t r0, int32_t r1) {
     for (int32_t x = r0 + blockIdx.x; x < r1; x += gridDim.x) {
         const int64_t s = __ldg(&off[x]), e = __ldg(&off[x + 1]);
         for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x)
-            if (!slot_deleted(tomb, p)) abc::cc_unite(parent, x, __ldg(&adj[p]));
+            if (edge_kept(tomb, keep, p, x, __ldg(&adj[p]))) abc::cc_unite(parent, x, __ldg(&adj[p]));
     }
 }
 
 // rows [r0, r1): one warp per row
-__global__ void k_cc_hook_warp(const int64_t *off, const int32_t *adj, const uint32_t *tomb, int32_t *parent,
+__global__ void k_cc_hook_warp(const int64_t *off, const int32_t *adj, const uint32_t *tomb, const uint8_t *keep,
+                                int32_t *parent,
                                int32_t r0, int32_t r1) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -47,17 +54,18 @@ __global__ void k_cc_hook_warp(const int64_t *off, const int32_t *adj, const uin
     for (int64_t x = r0 + w0; x < r1; x += nw) {
         const int64_t s = __ldg(&off[x]), e = __ldg(&off[x + 1]);
         for (int64_t p = s + lane; p < e; p += 32)
-            if (!slot_deleted(tomb, p)) abc::cc_unite(parent, (int32_t)x, __ldg(&adj[p]));
+            if (edge_kept(tomb, keep, p, (int32_t)x, __ldg(&adj[p]))) abc::cc_unite(parent, (int32_t)x, __ldg(&adj[p]));
     }
 }
 
 // rows [r0, r1): one thread per row
-__global__ void k_cc_hook_thread(const int64_t *off, const int32_t *adj, const uint32_t *tomb, int32_t *parent,
+__global__ void k_cc_hook_thread(const int64_t *off, const int32_t *adj, const uint32_t *tomb, const uint8_t *keep,
+                                int32_t *parent,
                                  int32_t r0, int32_t r1) {
     for (int64_t x = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < r1; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = __ldg(&off[x]), e = __ldg(&off[x + 1]);
         for (int64_t p = s; p < e; ++p)
-            if (!slot_deleted(tomb, p)) abc::cc_unite(parent, (int32_t)x, __ldg(&adj[p]));
+            if (edge_kept(tomb, keep, p, (int32_t)x, __ldg(&adj[p]))) abc::cc_unite(parent, (int32_t)x, __ldg(&adj[p]));
     }
 }
 
@@ -87,9 +95,52 @@ __global__ void k_cc_emit(const int32_t *old2new, const int32_t *parent, const i
     }
 }
 
+// Community of vertex q: members of the core (alive[x]) in q's component of the core.
+__global__ void k_community(const int32_t *old2new, const int32_t *parent, const uint8_t *alive, int32_t q_internal,
+                            int32_t nU, int32_t nV, uint8_t *mask_u, uint8_t *mask_v, unsigned long long *size) {
+    const int64_t n = (int64_t)nU + nV;
+    const int32_t rq = abc::cc_find(const_cast<int32_t *>(parent), q_internal);
+    const bool qin = __ldg(&alive[q_internal]) != 0;
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = __ldg(&old2new[i]);
+        const uint8_t in = (qin && __ldg(&alive[x]) && abc::cc_find(const_cast<int32_t *>(parent), x) == rq) ? 1 : 0;
+        if (i < nU) mask_u[i] = in;
+        else mask_v[i - nU] = in;
+        c += in;
+    }
+    c = (unsigned long long)abc::warp_sum64((long long)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(size, c);
+}
+
 }  // namespace
 
-int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st) {
+int community_compute(abcore_ctx *ctx, const uint8_t *d_alive, int32_t q_internal, uint8_t *d_mask_u,
+                      uint8_t *d_mask_v, int64_t *size) {
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    int32_t *parent = nullptr;
+    unsigned long long *cnt = nullptr;
+    ABC_TRY(ctx->alloc(&parent, (size_t)std::max<int64_t>(n, 1), "community forest"));
+    int rc = ctx->alloc(&cnt, 1, "community size");
+    if (!rc) rc = cc_hook_base(ctx, parent, nullptr, ctx->stream, d_alive);
+    unsigned long long h = 0;
+    if (!rc) {
+        const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16));
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream);
+        k_community<<<gi, 256, 0, ctx->stream>>>(g.old2new, parent, d_alive, q_internal, g.nU, g.nV, d_mask_u, d_mask_v, cnt);
+        ctx->stats.launches++;
+        cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+        const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = ctx->cuda_fail(e, "community");
+    }
+    ctx->release(parent);
+    ctx->release(cnt);
+    if (!rc && size) *size = (int64_t)h;
+    return rc;
+}
+
+int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st, const uint8_t *keep) {
     const Graph &g = ctx->g;
     const int64_t n = g.n();
     const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16));
@@ -97,16 +148,16 @@ int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStr
     // U rows by length (internal U ids are sorted by non-increasing degree)
     const int32_t h = (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, CC_HUB), g.nU);
     const int32_t w = (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, CC_MEDIUM), g.nU);
-    if (h > 0) k_cc_hook_block<<<(unsigned)std::min<int64_t>(h, (int64_t)ctx->num_sms * 8), 256, 0, st>>>(g.off, g.adj, tomb, parent, 0, h);
+    if (h > 0) k_cc_hook_block<<<(unsigned)std::min<int64_t>(h, (int64_t)ctx->num_sms * 8), 256, 0, st>>>(g.off, g.adj, tomb, keep, parent, 0, h);
     if (w > h) {
         const int64_t warps = w - h;
         k_cc_hook_warp<<<(unsigned)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)ctx->num_sms * 16), 256, 0, st>>>(
-            g.off, g.adj, tomb, parent, h, w);
+            g.off, g.adj, tomb, keep, parent, h, w);
     }
     if (g.nU > w) {
         const int64_t rows = g.nU - w;
         k_cc_hook_thread<<<(unsigned)std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->num_sms * 16), 256, 0, st>>>(
-            g.off, g.adj, tomb, parent, w, g.nU);
+            g.off, g.adj, tomb, keep, parent, w, g.nU);
     }
     ctx->stats.launches += 4;
     ABC_CU(cudaGetLastError());

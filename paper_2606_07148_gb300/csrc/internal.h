@@ -251,6 +251,12 @@ int build_graph(abcore_ctx *ctx, Graph &g, int32_t nU, int32_t nV, int64_t m, co
                 const int32_t *d_ev, const int32_t *d_rank, int32_t maxrank);
 int csr_edges(abcore_ctx *ctx, const Graph &g, int32_t *d_eu, int32_t *d_ev);  // caller-id edge list
 
+// query.cu -- core size, alpha_offset (the paper's default query), community search
+int core_size(abcore_ctx *ctx, int32_t alpha, int32_t beta, int64_t *size);
+int alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_out);
+int community(abcore_ctx *ctx, int32_t q_internal, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
+              int64_t *size);
+
 // tune.cu -- autotuner
 int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint32_t what,
              double *best_ms);
@@ -286,7 +292,10 @@ void free_serve(abcore_ctx *ctx);
 int serve_components(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
 
 // components.cu -- connected components (union-find)
-int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st);
+int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st,
+                 const uint8_t *keep = nullptr);
+int community_compute(abcore_ctx *ctx, const uint8_t *d_alive, int32_t q_internal, uint8_t *d_mask_u,
+                      uint8_t *d_mask_v, int64_t *size);
 int cc_emit(abcore_ctx *ctx, int32_t *parent, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp, cudaStream_t st);
 int components_compute(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
 
