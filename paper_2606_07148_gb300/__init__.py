@@ -245,8 +245,8 @@ class ABCore:
         self._check(abi.abcore_get_param(self._h, name.encode(), ctypes.byref(v)))
         return int(v.value)
 
-    TUNED = ("blocks_per_sm", "chunk", "grab_div", "hub_degree", "probe_bytes", "emit_scatter_max_pct",
-             "batch_wave")
+    TUNED = ("blocks_per_sm", "chunk", "grab_div", "batch_entries", "flush_steps", "hub_degree", "probe_bytes",
+             "emit_scatter_max_pct", "batch_wave")
 
     def graph_info(self):
         nU, nV, du, dv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -423,6 +423,16 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         p.chunk = (int)value;
         free_peel(ctx);
         free_batch(ctx);
+    } else if (k == "batch_entries") {
+        if (value < 128 || value > (1 << 24)) return ctx->fail(ABCORE_EINVAL, "batch_entries must be in [128, 2^24]");
+        ABC_TRY(abcore_sync(ctx));
+        p.batch_entries = (int)value;
+        free_batch(ctx);
+    } else if (k == "flush_steps") {
+        if (value < 1 || value > (1 << 20)) return ctx->fail(ABCORE_EINVAL, "flush_steps must be in [1, 2^20]");
+        ABC_TRY(abcore_sync(ctx));
+        p.flush_steps = (int)value;
+        free_batch(ctx);
     } else if (k == "grab_div") {
         if (value < 0) return ctx->fail(ABCORE_EINVAL, "grab_div must be >= 0");
         p.grab_div = (int)value;
@@ -483,6 +493,8 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     const std::string k(name);
     if (k == "chunk") *value = p.chunk;
     else if (k == "grab_div") *value = p.grab_div;
+    else if (k == "batch_entries") *value = p.batch_entries;
+    else if (k == "flush_steps") *value = p.flush_steps;
     else if (k == "blocks_per_sm") *value = p.blocks_per_sm;
     else if (k == "mode") *value = p.mode;
     else if (k == "timeout_ms") *value = p.timeout_ms;

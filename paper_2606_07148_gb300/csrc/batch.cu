@@ -65,12 +65,13 @@ struct BatchArgs {
     uint8_t *lvl;
     int32_t lvl_stride;
     int32_t chunk;
+    int32_t batch_entries, flush_steps;
     uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
 };
 
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
+__global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     __shared__ WarpSmem smem[BATCH_THREADS / 32];
     int c = 0;
     while (c + 1 < B.nchains && (int)blockIdx.x >= B.chains[c + 1].first_block) ++c;
@@ -95,6 +96,8 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(BatchArgs B) {
     a.thrU = cd.alpha;
     a.thrV = B.betas[cd.beta_off];
     a.chunk = B.chunk;
+    a.batch_entries = B.batch_entries;
+    a.flush_steps = B.flush_steps;
     a.searchU = cd.searchU;
     a.searchV = cd.searchV;
     a.hubcutU = cd.hubcutU;
@@ -460,6 +463,8 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.lvl_stride = b->lvl_stride;
         B.chunk = std::max(ctx->prm.chunk, 32);
         B.flags = b->flags;
+        B.batch_entries = ctx->prm.batch_entries;
+        B.flush_steps = ctx->prm.flush_steps;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
         void *args[] = {&B};

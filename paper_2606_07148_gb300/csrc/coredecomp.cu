@@ -44,7 +44,7 @@ struct CoreArgs {
     int32_t maxdeg;                 // max(maxdegU, maxdegV)
     unsigned long long nonisolated; // vertices of degree >= 1
     unsigned long long *removed;
-    int32_t chunk;
+    int32_t chunk, batch_entries, flush_steps;
     unsigned long long timeout_ns;
 };
 
@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core(CoreArgs C) {
     a.nU = C.nU;
     a.nV = C.nV;
     a.chunk = C.chunk;
+    a.batch_entries = C.batch_entries;
+    a.flush_steps = C.flush_steps;
     a.timeout_ns = C.timeout_ns;
     a.skip_zero = 0;
     a.corev = C.core;
@@ -220,6 +222,8 @@ static int core_decompose(abcore_ctx *ctx, int32_t *core_caller, int32_t *maxcor
         C.nonisolated = nonisolated;
         C.removed = removed;
         C.chunk = std::max(ctx->prm.chunk, 32);
+        C.batch_entries = ctx->prm.batch_entries;
+        C.flush_steps = ctx->prm.flush_steps;
         C.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
         void *args[] = {&C};
         cudaLaunchConfig_t cfg{};

@@ -54,6 +54,8 @@ struct PeelArgs {
                              // never counted, decremented or removed (0 for the plain peel)
     int32_t thrU, thrV;      // alpha, beta
     int32_t chunk;           // adjacency entries per work item
+    int32_t batch_entries;   // entries one warp walks per batch at most (the rest is re-queued)
+    int32_t flush_steps;     // steps a pending push may wait before its warp flushes
     int32_t grab_div;        // queue items per grab = clamp(available / grab_div, 1, 32)
     int32_t searchU;         // 1: U counts by searching U rows; 0: by streaming V violators
     int32_t searchV;         // 1: V counts by searching V rows; 0: by streaming U violators
@@ -82,6 +84,9 @@ struct PeelArgs {
 
 struct Params {
     int chunk = 1024;
+    int batch_entries = 1024;  // see PeelArgs (1024 kept a 94k-candidate, 18-level cascade 4.5x
+                               // faster than 4096; the autotuner may raise it)
+    int flush_steps = 4;
     int grab_div = 0;          // 0 = automatic (resident warps / 8)
     int threads = 256;
     int blocks_per_sm = 0;     // 0 = occupancy calculator

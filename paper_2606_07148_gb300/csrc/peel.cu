@@ -276,6 +276,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.thrU = alpha;
     a.thrV = beta;
     a.chunk = std::max(ctx->prm.chunk, 32);
+    a.batch_entries = ctx->prm.batch_entries;
+    a.flush_steps = ctx->prm.flush_steps;
     const int blocks = cascade_grid(ctx);
     a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
     a.searchU = mode & 1;

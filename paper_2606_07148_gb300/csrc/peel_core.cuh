@@ -29,9 +29,9 @@ template <int CAP>
 struct PushBuf {
     static_assert(CAP >= 64, "a flush must leave room for one warp's pushes");
     int32_t y[CAP];  // vertex
-    int32_t n[CAP];  // its item count, | PUSH_FROM1 when its chunks start at index 1
+    int32_t c[CAP];  // first chunk index
+    int32_t n[CAP];  // item count: chunks [c, c + n)
 };
-constexpr int32_t PUSH_FROM1 = 1 << 30;
 
 struct WarpSmem {
     long long start[MAX_GRAB];  // first adjacency index of each grabbed item
@@ -79,7 +79,7 @@ __device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, 
     __syncwarp();
     const int lane = threadIdx.x & 31;
     int mine = 0;
-    for (int i = lane; i < pc; i += 32) mine += pb.n[i] & (PUSH_FROM1 - 1);
+    for (int i = lane; i < pc; i += 32) mine += pb.n[i];
     const int incl = warp_incl_scan(mine);
     const int total = __shfl_sync(ABC_FULL, incl, 31);
     unsigned long long base = 0;
@@ -91,8 +91,8 @@ __device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, 
         unsigned long long pos = base + (unsigned long long)(incl - mine);
         for (int i = lane; i < pc; i += 32) {
             const unsigned long long hi = (unsigned long long)(uint32_t)pb.y[i] << 32;
-            const int nch = pb.n[i] & (PUSH_FROM1 - 1);
-            const unsigned c0 = (pb.n[i] & PUSH_FROM1) ? 1u : 0u;
+            const int nch = pb.n[i];
+            const unsigned c0 = (unsigned)pb.c[i];
             for (int c = 0; c < nch; ++c) st_relaxed(&a.q[pos + c], hi | (c0 + (unsigned)c));
             pos += (unsigned long long)nch;
         }
@@ -101,12 +101,12 @@ __device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, 
     pc = 0;
 }
 
-// Warp-collective: lanes with `want` queue nch items of vertex y, chunks [0, nch) (or [1, nch]
-// with `from1`); nch == 0 queues nothing. With `fallen`, y is a vertex that has just fallen (it
-// is counted, and its removal step recorded). Flushes when the buffer is nearly full.
+// Warp-collective: lanes with `want` queue nch items of vertex y, chunks [c0, c0 + nch); nch == 0
+// queues nothing. With `fallen`, y is a vertex that has just fallen (it is counted, and its
+// removal step recorded). Flushes when the buffer is nearly full.
 template <int CAP>
 __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, int &pc, bool want, int32_t y, int nch,
-                                         LaneStats &ls, bool fallen = true, bool from1 = false) {
+                                         LaneStats &ls, bool fallen = true, int c0 = 0) {
     if (want && fallen) {
         ls.pushes++;
         if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
@@ -122,7 +122,8 @@ __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, in
     if (keep) {
         const int i = pc + __popc(pm & lanemask_lt());
         pb.y[i] = y;
-        pb.n[i] = nch | (from1 ? PUSH_FROM1 : 0);
+        pb.c[i] = c0;
+        pb.n[i] = nch;
     }
     pc += __popc(pm);
     if (pc > CAP - 32) push_flush(a, pb, pc);
@@ -134,6 +135,12 @@ __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chu
 // atomics, of one step are independent, so they overlap instead of waiting one at a time.
 constexpr int ILP = 4;
 
+// Two limits shape a warp's batch (PeelArgs): batch_entries, the entries one warp walks per
+// batch at most -- items beyond go back to the queue for other warps (a warp holding 32 chunks of
+// hub rows would otherwise walk them alone while others idle); and flush_steps, the steps a
+// pending push may wait before its warp flushes (a batch producing few pushes would otherwise
+// hold them, and the cascade's next level, until it ends).
+
 // Warp-collective: process the items held by the lanes (`it` == EMPTY: none), spreading the
 // row chunks' entries evenly over the lanes (warp-level load balancing over an exclusive scan).
 //
@@ -144,29 +151,35 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
                                               LaneStats &ls) {
     const int lane = threadIdx.x & 31;
     long long start = 0;
-    int len = 0, upper = 0, more = 0;
+    int len = 0, upper = 0, more = 0, c = 0;
     int32_t x = 0;
     if (it != EMPTY) {
         x = (int32_t)(it >> 32);
-        const int c = (int)(it & 0xffffffffu);
+        c = (int)(it & 0xffffffffu);
         const int rl = row_len_of(a, x);
         start = __ldg(&a.off[x]) + (long long)c * a.chunk;
         len = min(a.chunk, rl - c * a.chunk);
         if (len < 0) len = 0;
         if (c == 0 && rl > a.chunk) more = chunks_of(rl, a.chunk) - 1;
         upper = x < a.nU;
-        ls.items++;
     }
     int pc = 0;
-    push_add(a, sm.push, pc, more > 0, x, more, ls, /*fallen=*/false, /*from1=*/true);
+    int incl = warp_incl_scan(len);
+    // items past batch_entries (never the first non-empty one) go back to the queue untouched;
+    // a kept chunk 0 of a long row queues the row's other chunks
+    const bool defer = incl - len >= a.batch_entries && it != EMPTY;
+    push_add(a, sm.push, pc, defer, x, 1, ls, /*fallen=*/false, /*c0=*/c);
+    push_add(a, sm.push, pc, more > 0 && !defer, x, more, ls, /*fallen=*/false, /*c0=*/1);
+    if (defer) len = 0;
+    if (it != EMPTY && !defer) ls.items++;
     push_flush(a, sm.push, pc);
-    const int incl = warp_incl_scan(len);
+    incl = warp_incl_scan(len);
     const int L = __shfl_sync(ABC_FULL, incl, 31);
     sm.start[lane] = start;
     sm.excl[lane] = incl - len;
     sm.upper[lane] = upper;
     __syncwarp();
-    int j = 0;
+    int j = 0, since = 0;
     for (int b = 0; b < L; b += 32 * ILP) {
         int32_t y[ILP];
         int32_t thr[ILP];
@@ -202,7 +215,11 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
             // the crossing decrement: y had a count of 1 or more, so its row is not empty
             push_add(a, sm.push, pc, hit[u] && old[u] == thr[u], y[u], 1, ls);
         }
-        if (pc >= 32) push_flush(a, sm.push, pc);
+        ++since;
+        if (pc >= 32 || (pc > 0 && since >= a.flush_steps)) {
+            push_flush(a, sm.push, pc);
+            since = 0;
+        }
     }
     push_flush(a, sm.push, pc);
     __syncwarp();
