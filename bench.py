@@ -161,11 +161,11 @@ def algorithmic_bytes(st):
     # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;
     # per entry 4 B; per decrement 8 B; per push 8 B queue write (the row length is read by
     # the consumer, inside the item's figure);
-    # emission: gather 1 B membership write + 4 B old2new + 1 B membership read + 1 B mask per
-    # vertex, plus 4 B count per candidate; scatter 4 B count per candidate
+    # emission: gather 4 B old2new + 1 B mask per vertex, plus 4 B count per candidate; scatter
+    # 4 B count per candidate
     dec_casc = st["decrements"] - dec_stream
     b[2] = (28 * st["items"] + 4 * st["entries"] + 8 * dec_casc + 8 * st["pushes"]
-            + 7 * st["emit_gathered"] + 4 * st["candidates"])
+            + 5 * st["emit_gathered"] + 4 * st["candidates"])
     return b
 
 

@@ -66,7 +66,6 @@ struct PeelArgs {
     const int32_t *old2new;  // [n] caller id (layer base + id) -> internal id
     const int32_t *new2old;  // [n] internal id -> caller per-layer id
     uint8_t *mask_u, *mask_v;
-    uint8_t *alive;          // [n] membership in internal order (emit 1: written, then gathered)
     int32_t emit;            // 0 none, 1 gather over all vertices, 2 scatter of live candidates
     int32_t skip_zero;       // 1: no decrements toward a layer whose threshold is 0
     // batched chains: a vertex queued during chain step `step` records it in
@@ -144,7 +143,6 @@ struct PeelWork {
                                        // before cascade, after cascade
     int next = 0, last = -1;
     uint8_t *stage = nullptr;      // [n] staging for host-pointer masks
-    uint8_t *alive = nullptr;      // [n] membership in internal order
     bool q_dirty = false;          // queue not known to be all-empty
     uint32_t *flags = nullptr;     // [grid * 32] per-block queue-closed flags (epochs)
     int flag_blocks = 0;

@@ -14,7 +14,7 @@
 //     the other layer form one contiguous slice of adj; it is streamed with 16-byte loads and
 //     every entry that hits a candidate decrements it (the paper's first peel round).
 //  3. k_cascade: the work-queue cascade (peel_core.cuh), then each warp writes its share of
-//     the masks in the caller's ids.
+//     the masks in the caller's ids (gathering each caller id's count through old2new).
 #include <algorithm>
 #include <cmath>
 
@@ -91,8 +91,29 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
     if (!ok || a.emit == 0) return;
     const int64_t n = (int64_t)a.nU + a.nV;
     if (a.emit == 1) {
-        // membership in internal order, coalesced; k_emit gathers it into the caller's order
-        for (int64_t x = gw * 32 + lane; x < n; x += nw * 32) a.alive[x] = alive_of(a, (int32_t)x) ? 1 : 0;
+        // gather in the caller's order: every count is final once the queue has closed. Each
+        // lane keeps EMIT_ILP independent id -> count -> mask chains in flight (this grid is
+        // small: one lane per chain would wait out every round trip in turn).
+        constexpr int EMIT_ILP = 8;
+        const int64_t stride = nw * 32;
+        for (int64_t i0 = gw * 32 + lane; i0 < n; i0 += stride * EMIT_ILP) {
+            int32_t x[EMIT_ILP];
+#pragma unroll
+            for (int k = 0; k < EMIT_ILP; ++k) {
+                const int64_t i = i0 + k * stride;
+                x[k] = i < n ? __ldg(&a.old2new[i]) : 0;
+            }
+            uint8_t v[EMIT_ILP];
+#pragma unroll
+            for (int k = 0; k < EMIT_ILP; ++k) v[k] = (i0 + k * stride < n && alive_of(a, x[k])) ? 1 : 0;
+#pragma unroll
+            for (int k = 0; k < EMIT_ILP; ++k) {
+                const int64_t i = i0 + k * stride;
+                if (i >= n) break;
+                if (i < a.nU) a.mask_u[i] = v[k];
+                else a.mask_v[i - a.nU] = v[k];
+            }
+        }
     } else {
         const int64_t P = (int64_t)a.pU + a.pV;
         for (int64_t p = gw * 32 + lane; p < P; p += nw * 32) {
@@ -103,18 +124,6 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
                 else a.mask_v[o] = 1;
             }
         }
-    }
-}
-
-// Masks in the caller's ids from the internal-order membership bytes (an L2-resident table).
-__global__ void __launch_bounds__(256) k_emit(const int32_t *__restrict__ old2new, const uint8_t *__restrict__ alive,
-                                              int32_t nU, int32_t nV, uint8_t *__restrict__ mask_u,
-                                              uint8_t *__restrict__ mask_v) {
-    const int64_t n = (int64_t)nU + nV;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t v = alive[__ldg(&old2new[i])];
-        if (i < nU) mask_u[i] = v;
-        else mask_v[i - nU] = v;
     }
 }
 
@@ -150,7 +159,6 @@ int peel_prepare(abcore_ctx *ctx) {
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
-    ABC_TRY(ctx->alloc(&w.alive, (size_t)std::max<int64_t>(n, 1), "membership bytes"));
     w.flag_blocks = cascade_grid(ctx);
     ABC_TRY(ctx->alloc(&w.flags, (size_t)w.flag_blocks * 32, "queue close flags"));
     ABC_CU(cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (size_t)w.flag_blocks * 32, ctx->stream));
@@ -173,7 +181,6 @@ void free_peel(abcore_ctx *ctx) {
     ctx->release(w.q);
     ctx->release(w.ctl);
     ctx->release(w.stage);
-    ctx->release(w.alive);
     ctx->release(w.flags);
     w.flag_blocks = 0;
     if (w.ctl_host) cudaFreeHost(w.ctl_host);
@@ -290,7 +297,6 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.new2old = g.new2old;
     a.mask_u = d_mask_u;
     a.mask_v = d_mask_v;
-    a.alive = w.alive;
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
@@ -355,11 +361,6 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][2], ctx->stream));
     k_cascade<<<blocks, 256, 0, ctx->stream>>>(a);
     ctx->stats.launches++;
-    if (a.emit == 1) {
-        const unsigned eg = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
-        k_emit<<<std::max(eg, 1u), 256, 0, ctx->stream>>>(g.old2new, w.alive, nU, nV, d_mask_u, d_mask_v);
-        ctx->stats.launches++;
-    }
     if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
     ABC_CU(cudaGetLastError());
     ABC_CU(cudaMemcpyAsync(w.ctl_host + slot, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, ctx->stream));
