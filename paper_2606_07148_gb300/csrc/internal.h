@@ -177,6 +177,7 @@ struct abcore_ctx {
     abcore_stats stats{};
     int64_t dev_bytes = 0, peak_bytes = 0;
     int cascade_blocks = 0;
+    int init_blocks = 0;     // resident k_init blocks (occupancy x SMs)
     BatchState *batch = nullptr;
     ServeState *serve = nullptr;
     bool pending_async = false;

@@ -326,7 +326,13 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     }
     if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
     if (Pu > 0) {
-        const int64_t gi = std::min<int64_t>((Pu + INIT_THREADS - 1) / INIT_THREADS, (int64_t)ctx->num_sms * 32);
+        // at most the blocks that fit at once: each lane then walks several candidates
+        if (ctx->init_blocks <= 0) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_init, INIT_THREADS, 0);
+            ctx->init_blocks = std::max(per_sm, 1) * ctx->num_sms;
+        }
+        const int64_t gi = std::min<int64_t>((Pu + INIT_THREADS - 1) / INIT_THREADS, ctx->init_blocks);
         k_init<<<(unsigned)std::max<int64_t>(gi, 1), INIT_THREADS, 0, ctx->stream>>>(a);
         si.has_init = true;
         ctx->stats.launches++;

@@ -426,49 +426,63 @@ __device__ __forceinline__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl
 template <int CAP>
 __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, int64_t t0, int64_t nthreads,
                                            LaneStats &ls, unsigned long long &probes, unsigned long long &inits) {
+    // each lane takes INIT_ILP candidates per pass, so their offset loads are in flight together
+    constexpr int INIT_ILP = 4;
     const int64_t nu = (int64_t)a.pU - a.cU, P = nu + (a.pV - a.cV);  // uncertain candidates
     const int lane = threadIdx.x & 31;
     int pc = 0;
-    for (int64_t b = t0 - lane; b < P; b += nthreads) {
-        const int64_t i = b + lane;
-        bool viol = false;
-        int32_t x = 0;
-        int nch = 0;
-        if (i < P) {
-            x = i < nu ? (int32_t)(a.cU + i) : (int32_t)(a.nU + a.cV + (i - nu));
-            const bool upper = x < a.nU;
-            const int64_t s = __ldg(&a.off[x]), e = __ldg(&a.off[x + 1]);
-            int len;
-            const bool hubx = upper ? x < a.hubcutU : x - a.nU < a.hubcutV;
-            if ((upper ? a.searchU : a.searchV) || hubx) {
-                const int32_t bound = upper ? a.nU + a.pV : a.pU;
-                if (e == s) {
-                    len = 0;
-                } else if (__ldg(&a.adj[e - 1]) < bound) {
-                    len = (int)(e - s);
-                    probes++;
-                } else {
-                    int64_t lo = s, hi = e - 1;  // adj[hi] >= bound
-                    probes++;
-                    while (lo < hi) {
-                        const int64_t mid = (lo + hi) >> 1;
-                        probes++;
-                        if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    len = (int)(lo - s);
-                }
-            } else {
-                len = (int)(e - s);
+    for (int64_t b = t0 - lane; b < P; b += nthreads * INIT_ILP) {
+        int32_t x[INIT_ILP];
+        int64_t s[INIT_ILP], e[INIT_ILP];
+#pragma unroll
+        for (int k = 0; k < INIT_ILP; ++k) {
+            const int64_t i = b + lane + k * nthreads;
+            x[k] = -1;
+            s[k] = e[k] = 0;
+            if (i < P) {
+                x[k] = i < nu ? (int32_t)(a.cU + i) : (int32_t)(a.nU + a.cV + (i - nu));
+                s[k] = __ldg(&a.off[x[k]]);
+                e[k] = __ldg(&a.off[x[k] + 1]);
             }
-            a.cnt[x] = len;
-            a.plen[x] = len;
-            inits++;
-            const int32_t thr = upper ? a.thrU : a.thrV;
-            viol = len < thr;
-            nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
         }
-        push_add(a, pb, pc, viol, x, nch, ls);
+#pragma unroll
+        for (int k = 0; k < INIT_ILP; ++k) {
+            bool viol = false;
+            int nch = 0;
+            if (x[k] >= 0) {
+                const bool upper = x[k] < a.nU;
+                int len;
+                const bool hubx = upper ? x[k] < a.hubcutU : x[k] - a.nU < a.hubcutV;
+                if ((upper ? a.searchU : a.searchV) || hubx) {
+                    // candidate neighbours form the row's prefix below the other layer's bound
+                    const int32_t bound = upper ? a.nU + a.pV : a.pU;
+                    if (e[k] == s[k]) {
+                        len = 0;
+                    } else if (__ldg(&a.adj[e[k] - 1]) < bound) {
+                        len = (int)(e[k] - s[k]);
+                        probes++;
+                    } else {
+                        int64_t lo = s[k], hi = e[k] - 1;  // adj[hi] >= bound
+                        probes++;
+                        while (lo < hi) {
+                            const int64_t mid = (lo + hi) >> 1;
+                            probes++;
+                            if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        len = (int)(lo - s[k]);
+                    }
+                } else {
+                    len = (int)(e[k] - s[k]);
+                }
+                a.cnt[x[k]] = len;
+                a.plen[x[k]] = len;
+                inits++;
+                viol = len < (upper ? a.thrU : a.thrV);
+                nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
+            }
+            push_add(a, pb, pc, viol, x[k], nch, ls);
+        }
     }
     push_flush(a, pb, pc);
 }
