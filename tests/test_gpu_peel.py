@@ -246,7 +246,7 @@ def test_autotune_keeps_results_exact():
     best, chosen = core.autotune(pairs)
     assert best > 0
     assert chosen["blocks_per_sm"] in (0, 2, 3) and chosen["chunk"] in (256, 512, 1024, 2048)
-    assert chosen["hub_degree"] in (0, 64, 256, 1024) and chosen["probe_bytes"] in (16, 32, 64)
+    assert chosen["hub_degree"] in (0, 64, 256, 1024) and chosen["probe_bytes"] in (12, 16, 24, 32, 64)
     for a, b in pairs + [(1, 7), (4, 4)]:
         mu, mv = core.compute(a, b)
         wu, wv = oracle.peel(nU, nV, off, adj, a, b)
