@@ -171,7 +171,7 @@ def algorithmic_bytes(st):
 
 def source_digest():
     h = hashlib.sha256()
-    for fn in ("peel.cu", "peel_core.cuh", "device.cuh", "internal.h"):
+    for fn in ("peel.cu", "batch.cu", "peel_core.cuh", "device.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2606_07148_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
