@@ -66,6 +66,7 @@ struct BatchArgs {
     int32_t lvl_stride;
     int32_t chunk;
     int32_t batch_entries, flush_steps;
+    int32_t packed;          // 16-bit counts (every degree below 2^16)
     uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     a.off = B.off;
     a.adj = B.adj;
     a.cnt = mem.cnt;
+    a.packed = B.packed;
     a.plen = mem.plen;
     a.q = mem.q;
     a.qcap = B.qcap;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
             int nch = 0;
             if (i < cd.pV0) {
                 x = (int32_t)(B.nU + i);
-                const int c = __ldcg(&a.cnt[x]);
+                const int c = abc::cnt_load(a, x);
                 viol = c >= prev && c < a.thrV;
                 if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
             }
@@ -391,6 +393,11 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
     return ABCORE_OK;
 }
 
+// Counts of the batch's chains are 16-bit when every degree fits (parameter "packed_counts").
+static bool batch_packed(const abcore_ctx *ctx) {
+    return ctx->prm.packed_counts && std::max(ctx->g.maxdegU, ctx->g.maxdegV) <= 65535;
+}
+
 // Chain workspaces: counts, queue, control block and barrier per concurrent chain, plus lvl.
 static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     const Graph &g = ctx->g;
@@ -412,14 +419,14 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     b->nmem = 0;
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
-    const double per_chain = 8.0 * n + 8.0 * qcap + 1.0 * n;  // counts + prefixes, queue, levels
+    const double per_chain = (batch_packed(ctx) ? 6.0 : 8.0) * n + 8.0 * qcap + 1.0 * n;  // counts + prefixes, queue, levels
     int fit = (int)std::max(1.0, 0.6 * (double)freeb / per_chain);
     const int chains = std::max(1, std::min(want_chains, fit));
     b->qcap = qcap;
     b->mem.resize(chains);
     for (int c = 0; c < chains; ++c) {
         ChainMem &m = b->mem[c];
-        ABC_TRY(ctx->alloc(&m.cnt, (size_t)std::max<int64_t>(n, 1), "batch counts"));
+        ABC_TRY(ctx->alloc(&m.cnt, (size_t)(batch_packed(ctx) ? n / 2 + 1 : std::max<int64_t>(n, 1)), "batch counts"));
         ABC_TRY(ctx->alloc(&m.plen, (size_t)std::max<int64_t>(n, 1), "batch prefixes"));
         ABC_TRY(ctx->alloc(&m.q, (size_t)qcap, "batch queue"));
         ABC_TRY(ctx->alloc(&m.ctl, 1, "batch control"));
@@ -464,6 +471,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.chunk = std::max(ctx->prm.chunk, 32);
         B.flags = b->flags;
         B.batch_entries = ctx->prm.batch_entries;
+        B.packed = batch_packed(ctx) ? 1 : 0;
         B.flush_steps = ctx->prm.flush_steps;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;

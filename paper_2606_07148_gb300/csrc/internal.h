@@ -43,7 +43,9 @@ enum {
 struct PeelArgs {
     const int64_t *off;      // [n+1] row offsets, internal unified ids
     const int32_t *adj;      // [2m] neighbours, each row ascending
-    int32_t *cnt;            // [n] count of live candidate neighbours (the atomic target)
+    int32_t *cnt;            // [n] count of live candidate neighbours (the atomic target); with
+                             // `packed`, n uint16 counts, two per 32-bit word
+    int32_t packed;
     int32_t *plen;           // [n] row prefix a removed candidate walks (candidate neighbours)
     unsigned long long *q;   // [qcap] work queue of (vertex << 32 | chunk); ~0 = empty slot
     long long qcap;
@@ -86,6 +88,7 @@ struct Params {
     int batch_entries = 1024;  // see PeelArgs (1024 kept a 94k-candidate, 18-level cascade 4.5x
                                // faster than 4096; the autotuner may raise it)
     int flush_steps = 4;
+    int packed_counts = 1;     // batch chains keep 16-bit counts when every degree fits
     int grab_div = 0;          // 0 = automatic (resident warps / 8)
     int threads = 256;
     int blocks_per_sm = 0;     // 0 = occupancy calculator

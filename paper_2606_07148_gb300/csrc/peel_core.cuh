@@ -65,6 +65,28 @@ __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper
     return y < a.pU && y >= a.cU;
 }
 
+// Counts, as int32 or (packed, when every degree fits 16 bits) as uint16 halves of 32-bit words:
+// half the footprint keeps more of them in L2. A packed decrement subtracts from the word holding
+// the count; a count is never decremented below zero (each decrement stands for a distinct live
+// neighbour falling), so no borrow crosses into the other half.
+__device__ __forceinline__ int cnt_load(const PeelArgs &a, int32_t x) {
+    return a.packed ? (int)__ldcg(reinterpret_cast<const unsigned short *>(a.cnt) + x) : __ldcg(&a.cnt[x]);
+}
+__device__ __forceinline__ void cnt_store(const PeelArgs &a, int32_t x, int v) {
+    if (a.packed) reinterpret_cast<unsigned short *>(a.cnt)[x] = (unsigned short)v;
+    else a.cnt[x] = v;
+}
+__device__ __forceinline__ int cnt_dec(const PeelArgs &a, int32_t x) {  // returns the old count
+    if (!a.packed) return atomicSub(&a.cnt[x], 1);
+    const unsigned sh = (unsigned)(x & 1) << 4;
+    const unsigned old = atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (x >> 1), 1u << sh);
+    return (int)((old >> sh) & 0xffffu);
+}
+__device__ __forceinline__ void cnt_dec_noret(const PeelArgs &a, int32_t x) {
+    if (!a.packed) atomicAdd(&a.cnt[x], -1);
+    else atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (x >> 1), 1u << ((unsigned)(x & 1) << 4));
+}
+
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in
 // cp[x].y (the full degree when its layer's counts came from the full rows).
 __device__ __forceinline__ int row_len_of(const PeelArgs &a, int32_t y) { return __ldcg(&a.plen[y]); }
@@ -208,7 +230,7 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
             }
         }
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) old[u] = hit[u] ? atomicSub(&a.cnt[y[u]], 1) : 0;
+        for (int u = 0; u < ILP; ++u) old[u] = hit[u] ? cnt_dec(a, y[u]) : 0;
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (hit[u]) ls.decs++;
@@ -475,7 +497,7 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                 } else {
                     len = (int)(e[k] - s[k]);
                 }
-                a.cnt[x[k]] = len;
+                cnt_store(a, x[k], len);
                 a.plen[x[k]] = len;
                 inits++;
                 viol = len < (upper ? a.thrU : a.thrV);
@@ -494,7 +516,7 @@ __device__ __forceinline__ void stream_entry(const PeelArgs &a, int32_t y, bool 
                                              LaneStats &ls) {
     int32_t thr = 0;
     if (valid && cand_of(a, y, from_upper, thr) && (thr > 0 || !a.skip_zero) && !stream_skips(a, y, from_upper)) {
-        atomicAdd(&a.cnt[y], -1);
+        cnt_dec_noret(a, y);
         ls.decs++;
     }
 }
@@ -564,7 +586,7 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
         int nch = 0;
         if (i < total) {
             x = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
-            const int c = __ldcg(&a.cnt[x]);
+            const int c = cnt_load(a, x);
             viol = c < (x < a.nU ? a.thrU : a.thrV);
             if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
             scanned++;

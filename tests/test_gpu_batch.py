@@ -112,3 +112,17 @@ def test_batch_mid_size_power_law():
     pairs = synth.grid_pairs(8, 1, 1024)
     _check_batch(core, nU, nV, off, adj, pairs)
     core.close()
+
+
+def test_batch_with_32_bit_counts(small):
+    # the chains keep 16-bit counts whenever every degree fits; the 32-bit path must agree
+    nU, nV, eu, ev, off, adj = small
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    pairs = synth.grid_pairs(8, 1, 64)
+    mu16, mv16 = _check_batch(core, nU, nV, off, adj, pairs)
+    core.set_param("packed_counts", 0)
+    assert core.get_param("packed_counts") == 0
+    mu32, mv32 = _check_batch(core, nU, nV, off, adj, pairs)
+    assert np.array_equal(mu16, mu32) and np.array_equal(mv16, mv32)
+    core.close()
