@@ -23,6 +23,7 @@ constexpr unsigned long long EMPTY = ~0ull;
 // one close flag per block, each on its own 128-byte line
 constexpr int FLAG_STRIDE = 32;
 constexpr int MAX_GRAB = 32;
+constexpr int LOCAL_ROUNDS = 256;  // batches one warp may chain on its own pushes (see cascade_loop)
 
 // Per-warp buffer of fallen vertices waiting to be queued (see push_add).
 template <int CAP>
@@ -169,8 +170,10 @@ constexpr int ILP = 4;
 // A vertex that falls during the cascade is queued as one item, chunk 0; whoever takes chunk 0
 // of a row longer than one chunk queues the row's other chunks. (The pusher would otherwise
 // have to read the fallen vertex's row length, one more dependent memory round trip per push.)
+//
+// Pushes still buffered when the batch ends are left in sm.push (pc entries) for the caller.
 __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long it, WarpSmem &sm,
-                                              LaneStats &ls) {
+                                              LaneStats &ls, int &pc) {
     const int lane = threadIdx.x & 31;
     long long start = 0;
     int len = 0, upper = 0, more = 0, c = 0;
@@ -185,7 +188,6 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
         if (c == 0 && rl > a.chunk) more = chunks_of(rl, a.chunk) - 1;
         upper = x < a.nU;
     }
-    int pc = 0;
     int incl = warp_incl_scan(len);
     // items past batch_entries (never the first non-empty one) go back to the queue untouched;
     // a kept chunk 0 of a long row queues the row's other chunks
@@ -243,8 +245,29 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
             since = 0;
         }
     }
-    push_flush(a, sm.push, pc);
     __syncwarp();
+}
+
+// Warp-collective: if the buffered pushes make at most 32 items, hand lane l the l-th of them and
+// empty the buffer (true); otherwise leave the buffer alone (false).
+__device__ __forceinline__ bool take_local(WarpSmem &sm, int &pc, unsigned long long &it) {
+    const int lane = threadIdx.x & 31;
+    int mine = 0;
+    for (int i = lane; i < pc; i += 32) mine += sm.push.n[i];
+    const int total = __shfl_sync(ABC_FULL, warp_incl_scan(mine), 31);
+    if (total > 32) return false;
+    // entry i covers items [first_i, first_i + n_i) in buffer order
+    it = EMPTY;
+    int first = 0;
+    for (int i = 0; i < pc; ++i) {
+        const int nn = sm.push.n[i];
+        if (lane >= first && lane < first + nn)
+            it = ((unsigned long long)(uint32_t)sm.push.y[i] << 32) | (unsigned)(sm.push.c[i] + (lane - first));
+        first += nn;
+    }
+    __syncwarp();
+    pc = 0;
+    return true;
 }
 
 // `head` is set to CLOSED when the queue drains; a ticket grab that returns CLOSED or more ends
@@ -349,7 +372,20 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
         }
         const unsigned have = __ballot_sync(ABC_FULL, it != EMPTY);
         if (have != 0) {
-            process_items(a, it, sm, ls);
+            // Work-first: what a batch leaves queued, if one warp can take it all, this warp takes
+            // next, skipping the queue's round trip (in the deep, narrow levels of a cascade that
+            // round trip is most of each level's latency). The batch's slots count as done only
+            // after the whole chain, so the queue cannot look drained meanwhile.
+            int pc = 0;
+            process_items(a, it, sm, ls, pc);
+            for (int round = 0; pc > 0; ++round) {
+                unsigned long long nxt = EMPTY;
+                if (round >= LOCAL_ROUNDS || !take_local(sm, pc, nxt)) {
+                    push_flush(a, sm.push, pc);
+                    break;
+                }
+                process_items(a, nxt, sm, ls, pc);
+            }
             __threadfence();
             __syncwarp();
             if (lane == 0) atomicAdd(&a.ctl->done, (unsigned long long)__popc(have));
