@@ -313,6 +313,18 @@ def run_peel(args, rank, world, local):
                 "kernel_share": {KERNEL_NAMES[k]: round(kern_ms[k] / max(sum(kern_ms[:3]), 1e-9), 3)
                                  for k in (0, 1, 2)}}
 
+    # the cascade's other ceiling: with the counts in L2 its decrements are random 4-byte
+    # atomics with return, whose device-wide rate the library measures here
+    at_ret, at_noret = core.measure_atomics(32 << 20)
+    casc_decs = st["decrements"] - st["stream_decrements"]
+    dec_rate = casc_decs / (kern_ms[2] / 1e3) if kern_ms[2] > 0 else 0.0
+    l2_atomics = {"kernel": "k_cascade", "decrements_per_s": round(dec_rate / 1e9, 2),
+                  "peak_per_s": round(at_ret / 1e9, 2), "unit": "G/s",
+                  "frac": round(dec_rate / at_ret, 4) if at_ret > 0 else None,
+                  "peak_without_return": round(at_noret / 1e9, 2),
+                  "probe": "2^26 random atomicSub with return over a 32 MB int array (L2-resident), "
+                           "abcore_measure_atomics"}
+
     # end to end through the C ABI with host buffers (pinned): per step, the queries' thresholds
     # go in as call arguments and every mask comes back to the host inside the timed region
     host = [(torch.empty(nU, dtype=torch.uint8, pin_memory=True), torch.empty(nV, dtype=torch.uint8, pin_memory=True))
@@ -405,7 +417,7 @@ def run_peel(args, rank, world, local):
                          % ((8 * (nU + nV + 1) + 8 * m) / 1e9),
                    "timed_wall_s": round(t_wall, 4), "algorithm": "GCC (plain peel, Algorithm 1)",
                    "autotuned": tuned, "autotune_s": round(tune_s, 2), "params": args.param},
-        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "l2_atomics": l2_atomics,
         "cpu_baseline": cpu, "parity": parity, "gccplus": gccp,
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4)},
     }

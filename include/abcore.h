@@ -259,6 +259,14 @@ int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
 /* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown. */
 int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
 
+/* Throughput of random 32-bit atomicSub on this device, per second, with the old value returned
+ * (the cascade's crossing test needs it) and without: 2^26 operations over an int array of the
+ * largest power-of-two size up to array_bytes (in [4 KiB, 4 GiB]; below the L2's size the array
+ * stays in L2), best of three timed runs after one warm-up. This is the ceiling of a cascade
+ * whose counts sit in L2. Errors: EINVAL, ENOMEM, ECUDA. */
+int abcore_measure_atomics(abcore_ctx *ctx, int64_t array_bytes, double *with_return,
+                           double *without_return);
+
 /* Current value of a tuning parameter (the names abcore_set_param takes, except the actions
  * "reset_stats" and "debug_stall_slots"); EINVAL if unknown. */
 int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value);

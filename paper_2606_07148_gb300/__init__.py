@@ -145,6 +145,12 @@ class ABCore:
                                         b.ctypes.data_as(ctypes.c_void_p), what, ctypes.byref(best)))
         return best.value, {k: self.get_param(k) for k in self.TUNED}
 
+    def measure_atomics(self, array_bytes=32 << 20):
+        """Random 32-bit atomicSub throughput (per second), with and without the returned value."""
+        w, wo = ctypes.c_double(0), ctypes.c_double(0)
+        self._check(abi.abcore_measure_atomics(self._h, int(array_bytes), ctypes.byref(w), ctypes.byref(wo)))
+        return w.value, wo.value
+
     def sync(self):
         self._check(abi.abcore_sync(self._h))
 

@@ -32,7 +32,7 @@ ABCORE_DELETE = 1
 EXPORTED = [
     "abcore_create", "abcore_destroy", "abcore_last_error", "abcore_load_edges", "abcore_load_csr",
     "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_core_numbers", "abcore_autotune",
-    "abcore_alpha_offset", "abcore_community", "abcore_query_edge",
+    "abcore_alpha_offset", "abcore_community", "abcore_measure_atomics", "abcore_query_edge",
     "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
     "abcore_get_stats", "abcore_set_param", "abcore_get_param", "abcore_graph_info", "abcore_export_csr",
     "abcore_compute_static",
@@ -104,6 +104,8 @@ def load_library(path: str = LIB):
         "abcore_alpha_offset": ([_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "abcore_community": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                               ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32], ctypes.c_int),
+        "abcore_measure_atomics": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "abcore_core_numbers": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32], ctypes.c_int),
         "abcore_components": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32], ctypes.c_int),
         "abcore_query_edge": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
@@ -148,6 +150,7 @@ abcore_core_numbers = _fn("abcore_core_numbers")
 abcore_autotune = _fn("abcore_autotune")
 abcore_alpha_offset = _fn("abcore_alpha_offset")
 abcore_community = _fn("abcore_community")
+abcore_measure_atomics = _fn("abcore_measure_atomics")
 abcore_query_edge = _fn("abcore_query_edge")
 abcore_serve_start = _fn("abcore_serve_start")
 abcore_serve_submit = _fn("abcore_serve_submit")

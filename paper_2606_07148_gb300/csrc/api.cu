@@ -350,6 +350,16 @@ int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int
     return autotune(ctx, n, alphas, betas, what, best_ms);
 }
 
+int abcore_measure_atomics(abcore_ctx *ctx, int64_t array_bytes, double *with_return, double *without_return) {
+    if (!ctx || !with_return || !without_return) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    if (array_bytes < 4096 || array_bytes > ((int64_t)4 << 30))
+        return ctx->fail(ABCORE_EINVAL, "array_bytes must be in [4 KiB, 4 GiB]");
+    ABC_TRY(peel_finish(ctx));
+    return measure_atomics(ctx, array_bytes, with_return, without_return);
+}
+
 int abcore_sync(abcore_ctx *ctx) {
     if (!ctx) return ABCORE_EINVAL;
     ABC_CU(cudaSetDevice(ctx->device));

@@ -264,6 +264,9 @@ int alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_out);
 int community(abcore_ctx *ctx, int32_t q_internal, int32_t alpha, int32_t beta, uint8_t *d_mask_u, uint8_t *d_mask_v,
               int64_t *size);
 
+// probe.cu -- random-atomic throughput
+int measure_atomics(abcore_ctx *ctx, int64_t array_bytes, double *with_return, double *without_return);
+
 // tune.cu -- autotuner
 int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas, uint32_t what,
              double *best_ms);
