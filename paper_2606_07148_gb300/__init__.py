@@ -234,6 +234,17 @@ class ABCore:
         self._check(abi.abcore_serve_poll(self._h, ctypes.cast(out, ctypes.c_void_p), max_n, ctypes.byref(got)))
         return out[:got.value]
 
+    RESP_DTYPE = np.dtype([("seq", "<u8"), ("tag", "<u8"), ("status", "<i4"), ("in_core", "u1"),
+                           ("u_in", "u1"), ("v_in", "u1"), ("pad", "u1")])
+
+    def serve_poll_into(self, buf):
+        """Poll into a reusable numpy array of RESP_DTYPE; returns the filled prefix (a view).
+        Creates no Python object per response, so a long stream leaves nothing for the
+        garbage collector to walk."""
+        got = ctypes.c_int32(0)
+        self._check(abi.abcore_serve_poll(self._h, ctypes.c_void_p(buf.ctypes.data), len(buf), ctypes.byref(got)))
+        return buf[:got.value]
+
     def serve_stop(self):
         self._check(abi.abcore_serve_stop(self._h))
 
