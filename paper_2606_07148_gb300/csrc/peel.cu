@@ -5,16 +5,22 @@
 // are the prefixes P_U = [0, pU) and P_V = [nU, nU + pV). Every other vertex violates at once
 // (the scan phase of Algorithm 1) and is never looked at individually.
 //
-// Three launches:
+// Up to four launches:
 //  1. k_init: for each candidate x, its count of live candidate neighbours. Per layer, either
 //     (search) a binary search in x's sorted row for the candidate boundary of the other layer,
 //     which equals the count left after removing all initial violators; or (stream) the full
 //     degree, corrected by step 2. Candidates already below their bound are queued.
 //  2. k_stream (only for layers counted by full degree): the rows of the initial violators of
 //     the other layer form one contiguous slice of adj; it is streamed with 16-byte loads and
-//     every entry that hits a candidate decrements it (the paper's first peel round).
+//     every entry that hits a candidate decrements it (the paper's first peel round), then
+//     k_scan queues the candidates whose count the stream took below their bound.
 //  3. k_cascade: the work-queue cascade (peel_core.cuh), then each warp writes its share of
 //     the masks in the caller's ids (gathering each caller id's count through old2new).
+//
+// With core numbers prepared (coredecomp.cu), the same launches run pruned (Algorithm 2) on the
+// core-ordered copy of the graph: a prefix of each layer is certain to be in the core and is
+// never counted, decremented or removed (PeelArgs cU, cV), and the candidates are the vertices
+// with core number >= min(alpha, beta).
 #include <algorithm>
 #include <cmath>
 
