@@ -259,3 +259,12 @@ def test_autotune_keeps_results_exact():
         wu, wv = oracle.peel(nU, nV, off, adj, a, b)
         assert np.array_equal(bu[i].cpu().numpy(), wu) and np.array_equal(bv[i].cpu().numpy(), wv)
     core.close()
+
+
+def test_measure_atomics_reports_rates():
+    core = ABCore(0)
+    w, wo = core.measure_atomics(8 << 20)
+    assert w > 1e9 and wo > 1e9  # at least a billion random atomics per second on any GB300
+    with pytest.raises(ABCoreError):
+        core.measure_atomics(16)
+    core.close()
