@@ -9,7 +9,8 @@ input edges per second per peel, summed over the queries of a step and over all 
 
 Other workloads (--workload): "billion-100Mx50M-1500M" (the (64,64) single peel on the 1.5B-edge
 graph), "batch-20Mx10M-500M" / "billion-batch" (batched cores/s), "serve-10Mx5M-200M"
-(edge-query latency). --impl reference times the CPU oracle on the same workload.
+(edge-query latency), "sweep" or "sweep:<graph workload>" (the paper's alpha/beta sensitivity
+protocol, GCC against GCC+). --impl reference times the CPU oracle on the same workload.
 
 One JSON line is printed by rank 0.
 """
@@ -673,6 +674,72 @@ def run_serve(args, rank, world, local):
     return line
 
 
+def run_sweep(args, rank, world, local):
+    """The paper's alpha/beta sensitivity protocol (Section 6): delta = the largest core number;
+    fix beta = 0.5 delta and vary alpha = c delta, then fix alpha = 0.5 delta and vary
+    beta = c delta, c = 0.1 .. 0.9; each query timed with the plain peel (GCC) and with the
+    core-number pruning (GCC+), L2 flushed before each run."""
+    import torch
+    from paper_2606_07148_gb300 import ABCore
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    base = args.workload.split(":", 1)[1] if ":" in args.workload else "peel-4Mx2M-80M"
+    spec, nU, nV, eu, ev = make_inputs(base, dev)
+    m = spec["m"]
+    core = ABCore(local)
+    core.load_edges(nU, nV, eu, ev)
+    del eu, ev
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, _, delta = core.core_numbers()
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t) * 1e3
+    ou = torch.empty(nU, dtype=torch.uint8, device=dev)
+    ov = torch.empty(nV, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(a, b, algo):
+        core.set_param("algo", algo)
+        core.compute(a, b, ou, ov)
+        best = 1e9
+        for i in range(max(args.steps, 1)):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            core.compute(a, b, ou, ov, asynchronous=True)
+            e1.record()
+            core.sync()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return round(best, 4)
+
+    cs = [round(0.1 * i, 1) for i in range(1, 10)]
+    half = max(1, int(0.5 * delta))
+    rows = []
+    for fixed in ("beta", "alpha"):
+        for c in cs:
+            v = max(1, int(c * delta))
+            a, b = (v, half) if fixed == "beta" else (half, v)
+            g1, g2 = timed(a, b, 1), timed(a, b, 2)
+            rows.append({"vary": "alpha" if fixed == "beta" else "beta", "c": c, "alpha": a, "beta": b,
+                         "gcc_ms": g1, "gccplus_ms": g2})
+    clk = {"note": "not sampled for the sweep"}
+    total_gcc = sum(r["gcc_ms"] for r in rows)
+    line = {
+        "metric": "alpha/beta sweep: queries/s, plain peel", "value": round(len(rows) / (total_gcc / 1e3), 2),
+        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": round(total_gcc, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "sweep:" + base, "graph": describe(spec, base), "delta": delta,
+                   "core_numbers_ms": round(prep_ms, 2), "edges": m,
+                   "l2": "flushed before every timed query (256 MB write)"},
+        "gccplus_queries_per_s": round(len(rows) / (sum(r["gccplus_ms"] for r in rows) / 1e3), 2),
+        "queries": rows, "clocks": clk,
+    }
+    core.close()
+    return line
+
+
 def apply_params(core, args):
     for kv in args.param:
         k, v = kv.split("=", 1)
@@ -753,6 +820,8 @@ def main():
         barrier(world)
         if args.workload.startswith("batch") or args.workload == "billion-batch":
             line = run_batch(args, rank, world, local)
+        elif args.workload.startswith("sweep"):
+            line = run_sweep(args, rank, world, local)
         elif args.workload.startswith("serve"):
             line = run_serve(args, rank, world, local)
         else:
