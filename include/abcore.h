@@ -237,7 +237,8 @@ typedef struct {
  * if requests were processed one at a time, so answers do not depend on timing or batching.
  * Each target keeps its own device view of the updates; inserted edges live in a pool sized by
  * the "serve_inserts" parameter (default 2^20 inserts, 32 bytes each per target): once it is
- * full the loop stops with ABCORE_ENOMEM, reported by the next submit, poll or stop. */
+ * full the loop stops with ABCORE_ENOMEM, reported by the next submit, poll or stop; the
+ * session's view of the graph is then unusable and the context must be destroyed. */
 int abcore_serve_start(abcore_ctx *ctx, const int32_t *target_alphas, const int32_t *target_betas,
                        int32_t n_targets, int32_t ring_slots);
 

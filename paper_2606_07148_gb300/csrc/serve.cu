@@ -474,6 +474,10 @@ __global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
             const unsigned long long t0 = abc::now_ns();
             unsigned sl = 64;
             for (;;) {
+                if (abc::ld_relaxed_i32(A.err)) {  // an error (a full pool) ends the session
+                    state_s = 1;
+                    break;
+                }
                 const unsigned long long ex = abc::ld_relaxed(A.exit_at);
                 if (k >= ex) {  // the loop is closing at request count ex
                     state_s = 1;
@@ -481,10 +485,6 @@ __global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
                 }
                 const unsigned long long sub = ld_sys(A.submitted);
                 if (k < sub) break;
-                if (abc::ld_relaxed_i32(A.err)) {
-                    state_s = 1;
-                    break;
-                }
                 if (ld_sys_i32(A.stop) || abc::now_ns() - t0 > A.idle_ns) {
                     // stop request or idle spell: close the loop for every block at count `sub`,
                     // so no block handles a request the others skip; the host relaunches later

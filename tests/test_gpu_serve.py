@@ -204,3 +204,48 @@ def test_serve_rejects_bad_requests():
     assert all(r.status == abi.ABCORE_ENOENT for r in got)
     core.serve_stop()
     core.close()
+
+
+def test_inserted_edge_pool_exhaustion_is_reported():
+    # a tiny inserted-edge pool: the loop stops with ABCORE_ENOMEM (a status, not a fault) and
+    # the library stays usable afterwards
+    import time
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    eu, ev = eu.numpy(), ev.numpy()
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    core.set_param("serve_inserts", 16)
+    core.serve_start([(2, 2)], ring_slots=64)
+    present = set(zip(eu.tolist(), ev.tolist()))
+    rng = np.random.default_rng(1)
+    ins = []
+    while len(ins) < 2000:
+        u, v = int(rng.integers(nU)), int(rng.integers(nV))
+        if (u, v) not in present:
+            present.add((u, v))
+            ins.append((u, v))
+    err = None
+    t0 = time.time()
+    k = 0
+    try:
+        while k < len(ins):
+            assert time.time() - t0 < 60
+            hi = min(len(ins), k + 32)
+            arr = (abi.abcore_req * (hi - k))()
+            for i, (u, v) in enumerate(ins[k:hi]):
+                arr[i].op, arr[i].u, arr[i].v, arr[i].target, arr[i].tag = abi.ABCORE_INSERT, u, v, 0, k + i
+            if core.serve_submit(arr) is not None:
+                k = hi
+            core.serve_poll(4096)
+        core.serve_stop()
+    except ABCoreError as e:
+        err = e
+    assert err is not None and err.code == abi.ABCORE_ENOMEM
+    core.close()
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    mu, mv = core.compute(2, 3)
+    off, adj = oracle.build_csr(nU, nV, eu, ev)
+    wu, wv = oracle.peel(nU, nV, off, adj, 2, 3)
+    assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv)
+    core.close()
