@@ -147,7 +147,9 @@ def gpu_uuid(dev):
 # ------------------------------------------------------------------------------------------
 # roofline bookkeeping (per-unit algorithmic bytes; the figures are documented in the design doc)
 # ------------------------------------------------------------------------------------------
-KERNEL_NAMES = {0: "k_init", 1: "k_stream", 2: "k_cascade", 3: "k_batch", 4: "k_serve"}
+# kernel kinds as the library times them: 1 is the first round (the violator stream, the
+# no-return walk of the initial candidate violators, and the scan after them)
+KERNEL_NAMES = {0: "k_init", 1: "k_stream+k_round0+k_scan", 2: "k_cascade", 3: "k_batch", 4: "k_serve"}
 
 
 def algorithmic_bytes(st):
@@ -156,8 +158,8 @@ def algorithmic_bytes(st):
     # init: per candidate 8 B of offsets (consecutive rows share them) + 8 B count/prefix write;
     # 4 B per word probed by the boundary search
     b[0] = 16 * st["init_vertices"] + 4 * st["search_probes"]
-    # stream (+ the scan after it): 4 B per streamed entry + 8 B per counter decrement (4 B read
-    # + 4 B write) + 4 B per candidate count checked by the scan
+    # first round (stream or round0, + the scan after it): 4 B per streamed entry + 8 B per
+    # counter decrement (4 B read + 4 B write) + 4 B per candidate count checked by the scan
     dec_stream = st["stream_decrements"]
     b[1] = 4 * st["stream_entries"] + 8 * dec_stream + 4 * st.get("scanned", 0)
     # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;

@@ -443,6 +443,10 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         ABC_TRY(abcore_sync(ctx));
         p.packed_counts = (int)value;
         free_batch(ctx);
+    } else if (k == "round0") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "round0 must be 0 or 1");
+        ABC_TRY(abcore_sync(ctx));
+        p.round0 = (int)value;
     } else if (k == "flush_steps") {
         if (value < 1 || value > (1 << 20)) return ctx->fail(ABCORE_EINVAL, "flush_steps must be in [1, 2^20]");
         ABC_TRY(abcore_sync(ctx));
@@ -511,6 +515,7 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "batch_entries") *value = p.batch_entries;
     else if (k == "flush_steps") *value = p.flush_steps;
     else if (k == "packed_counts") *value = p.packed_counts;
+    else if (k == "round0") *value = p.round0;
     else if (k == "blocks_per_sm") *value = p.blocks_per_sm;
     else if (k == "mode") *value = p.mode;
     else if (k == "timeout_ms") *value = p.timeout_ms;

@@ -24,6 +24,8 @@ struct PeelCtl {
     unsigned long long pad2[15];
     int err;                   // first error code (0 = none)
     int pad3[31];
+    unsigned long long l0n;    // candidates found below their bound by the count init (round0)
+    unsigned long long pad4[15];
     unsigned long long st[12]; // stat counters, see ST_* below
 };
 enum {
@@ -75,6 +77,11 @@ struct PeelArgs {
     uint8_t *lvl;
     int32_t lvl_stride, lvl_col, step;
     int32_t *corev;          // if set, a vertex queued during `step` gets corev[vertex] = step
+    // round0: the count init lists its violators in l0 (not the queue); k_round0 walks their rows
+    // with atomics that return nothing, and the scan then queues every other candidate below its
+    // bound (see peel.cu)
+    int32_t round0;
+    int32_t *l0;
     unsigned long long *removed;  // if set, counts the vertices queued
     // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
     // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
@@ -89,6 +96,12 @@ struct Params {
                                // faster than 4096; the autotuner may raise it)
     int flush_steps = 4;
     int packed_counts = 1;     // batch chains keep 16-bit counts when every degree fits
+    int round0 = 0;            // single peel: walk the initial candidate violators' rows with
+                               // no-return atomics when a layer counts by search (k_round0), instead
+                               // of queueing them. Pays where the cascade is bound by atomic
+                               // throughput (1.5B edges, (64,64): 2.01 -> 1.74 ms); costs where it is
+                               // latency-bound (80M edges, (50,50): 0.30 -> 0.53 ms). The autotuner
+                               // decides per workload.
     int grab_div = 0;          // 0 = automatic (resident warps / 8)
     int threads = 256;
     int blocks_per_sm = 0;     // 0 = occupancy calculator
@@ -149,6 +162,7 @@ struct PeelWork {
     bool q_dirty = false;          // queue not known to be all-empty
     uint32_t *flags = nullptr;     // [grid * 32] per-block queue-closed flags (epochs)
     int flag_blocks = 0;
+    int32_t *l0 = nullptr;         // [n] initial candidate violators (round0)
     uint32_t epoch = 0;            // last cascade epoch handed out
 };
 

@@ -81,6 +81,71 @@ __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
     }
 }
 
+// round0: the rows of the candidates the count init found below their bound (listed in l0) --
+// the first peel round of Algorithm 1 for them -- walked with decrements that return nothing, as
+// the violator stream does; no crossing is looked for here, k_scan finds every candidate the
+// round took below its bound. Lane l of a warp takes listed vertex base + l and the warp balances
+// their rows' entries over its lanes.
+__global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
+    __shared__ long long s_start[256 / 32][32];
+    __shared__ int s_excl[256 / 32][32];
+    __shared__ int s_upper[256 / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nl0 = (int64_t)a.ctl->l0n;  // written by k_init, earlier on the stream
+    unsigned long long ents = 0, decs = 0;
+    for (int64_t g0 = gw * 32; g0 < nl0; g0 += nw * 32) {
+        int32_t x = -1;
+        int len = 0;
+        long long start = 0;
+        if (g0 + lane < nl0) {
+            x = __ldg(&a.l0[g0 + lane]);
+            len = __ldcg(&a.plen[x]);
+            start = __ldg(&a.off[x]);
+        }
+        const int incl = abc::warp_incl_scan(len);
+        const int L = __shfl_sync(ABC_FULL, incl, 31);
+        s_start[wib][lane] = start;
+        s_excl[wib][lane] = incl - len;
+        s_upper[wib][lane] = x >= 0 && x < a.nU;
+        __syncwarp();
+        int j = 0;
+        for (int b = 0; b < L; b += 32 * abc::ILP) {
+            int32_t y[abc::ILP];
+            int up[abc::ILP];
+#pragma unroll
+            for (int u = 0; u < abc::ILP; ++u) {
+                const int e = b + 32 * u + lane;
+                y[u] = -1;
+                up[u] = 0;
+                if (e < L) {
+                    while (j + 1 < 32 && s_excl[wib][j + 1] <= e) ++j;
+                    y[u] = abc::ld_adj(&a.adj[s_start[wib][j] + (e - s_excl[wib][j])]);
+                    up[u] = s_upper[wib][j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < abc::ILP; ++u) {
+                if (y[u] < 0) continue;
+                ents++;
+                int32_t t;
+                if (abc::cand_of(a, y[u], up[u] != 0, t) && (t > 0 || !a.skip_zero)) {
+                    abc::cnt_dec_noret(a, y[u]);
+                    decs++;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    ents = (unsigned long long)abc::warp_sum64((long long)ents);
+    decs = (unsigned long long)abc::warp_sum64((long long)decs);
+    if (lane == 0) {
+        if (ents) atomicAdd(&a.ctl->st[ST_STREAM], ents);
+        if (decs) atomicAdd(&a.ctl->st[ST_SDECS], decs);
+    }
+}
+
 __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
     if (x < a.nU) return x < a.pU && (x < a.cU || __ldcg(&a.cnt[x]) >= a.thrU);
     return x < a.nU + a.pV && (x < a.nU + a.cV || __ldcg(&a.cnt[x]) >= a.thrV);
@@ -162,6 +227,7 @@ int peel_prepare(abcore_ctx *ctx) {
     free_peel(ctx);
     ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(n, 1), "peel counts"));
     ABC_TRY(ctx->alloc(&w.plen, (size_t)std::max<int64_t>(n, 1), "peel prefixes"));
+    ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
@@ -184,6 +250,7 @@ void free_peel(abcore_ctx *ctx) {
     PeelWork &w = ctx->w;
     ctx->release(w.cnt);
     ctx->release(w.plen);
+    ctx->release(w.l0);
     ctx->release(w.q);
     ctx->release(w.ctl);
     ctx->release(w.stage);
@@ -306,6 +373,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
+    a.round0 = (ctx->prm.round0 && (a.searchU || a.searchV)) ? 1 : 0;
+    a.l0 = w.l0;
     a.flags = w.flags;
     a.flag_first = 0;
     a.flag_count = blocks;
@@ -355,15 +424,27 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             sb = cnt_ge(g.edgesU_ge, alpha);
             eb = g.m;
         }
-        if (ea > sa || eb > sb) {
+        const bool stream = ea > sa || eb > sb;
+        if (stream) {
             const int64_t work = ((ea - sa) + (eb - sb)) / 4 + 1;
             const int64_t gs = std::min<int64_t>((work + STREAM_THREADS - 1) / STREAM_THREADS,
                                                  (int64_t)ctx->num_sms * 16);
             k_stream<<<(unsigned)std::max<int64_t>(gs, 1), STREAM_THREADS, 0, ctx->stream>>>(a, sa, ea, sb, eb);
             si.has_stream = true;
             ctx->stats.launches++;
-            // the candidates counted by degree that the stream pushed below their bound
-            const int64_t ns = (a.searchU ? 0 : (int64_t)pU - a.hubcutU) + (a.searchV ? 0 : (int64_t)pV - a.hubcutV);
+        }
+        if (a.round0) {
+            // the initial candidate violators' rows (their count is below the bound, so each row
+            // is shorter than the bound)
+            const int64_t gr = std::min<int64_t>((Pu + 255) / 256, (int64_t)ctx->num_sms * 16);
+            k_round0<<<(unsigned)std::max<int64_t>(gr, 1), 256, 0, ctx->stream>>>(a);
+            si.has_stream = true;
+            ctx->stats.launches++;
+        }
+        if (stream || a.round0) {
+            // the candidates these first-round decrements took below their bound
+            const int64_t ns = a.round0 ? Pu
+                                        : (a.searchU ? 0 : (int64_t)pU - a.hubcutU) + (a.searchV ? 0 : (int64_t)pV - a.hubcutV);
             const int64_t gsc = std::min<int64_t>((ns + 255) / 256, (int64_t)ctx->num_sms * 16);
             k_scan<<<(unsigned)std::max<int64_t>(gsc, 1), 256, 0, ctx->stream>>>(a);
             ctx->stats.launches++;

@@ -539,7 +539,21 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                 viol = len < (upper ? a.thrU : a.thrV);
                 nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
             }
-            push_add(a, pb, pc, viol, x[k], nch, ls);
+            if (a.round0) {
+                // listed for k_round0 instead of queued
+                const unsigned vm = __ballot_sync(ABC_FULL, viol);
+                if (vm) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&a.ctl->l0n, (unsigned long long)__popc(vm));
+                    base = __shfl_sync(ABC_FULL, base, 0);
+                    if (viol) {
+                        a.l0[base + __popc(vm & lanemask_lt())] = x[k];
+                        ls.pushes++;
+                    }
+                }
+            } else {
+                push_add(a, pb, pc, viol, x[k], nch, ls);
+            }
         }
     }
     push_flush(a, pb, pc);
@@ -612,8 +626,10 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                                            LaneStats &ls, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
     int pc = 0;
-    const int64_t u0 = a.searchU ? a.pU : max(a.hubcutU, a.cU);  // U ids [u0, pU) counted by degree
-    const int64_t v0 = a.searchV ? a.pV : max(a.hubcutV, a.cV);  // V ids nU + [v0, pV)
+    // U ids [u0, pU) and V ids nU + [v0, pV): the candidates counted by degree, or with round0
+    // every uncertain candidate (the ones round0 already walked have plen below their bound)
+    const int64_t u0 = a.round0 ? a.cU : (a.searchU ? a.pU : max(a.hubcutU, a.cU));
+    const int64_t v0 = a.round0 ? a.cV : (a.searchV ? a.pV : max(a.hubcutV, a.cV));
     const int64_t nu = a.pU - u0, total = nu + (a.pV - v0);
     for (int64_t b = t0 - lane; b < total; b += nthreads) {
         const int64_t i = b + lane;
@@ -623,8 +639,13 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
         if (i < total) {
             x = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
             const int c = cnt_load(a, x);
-            viol = c < (x < a.nU ? a.thrU : a.thrV);
-            if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
+            const int thr = x < a.nU ? a.thrU : a.thrV;
+            viol = c < thr;
+            if (viol) {
+                const int pl = __ldcg(&a.plen[x]);
+                if (a.round0 && pl < thr) viol = false;  // an initial violator: round0 walked it
+                else nch = pl > 0 ? 1 : 0;               // chunk 0 (see process_items)
+            }
             scanned++;
         }
         push_add(a, pb, pc, viol, x, nch, ls);

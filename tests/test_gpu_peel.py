@@ -268,3 +268,28 @@ def test_measure_atomics_reports_rates():
     with pytest.raises(ABCoreError):
         core.measure_atomics(16)
     core.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_round0_first_round_without_returns(mode):
+    # the initial candidate violators' rows walked by k_round0 (no-return decrements, then a scan
+    # for what they took below the bound), in every mode with a searched layer, plain and pruned
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    core.set_param("round0", 1)
+    core.set_param("mode", mode)
+    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8)]
+    for a, b in pairs:
+        mu, mv = core.compute(a, b)
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (mode, a, b)
+    if mode == 3:
+        core.core_numbers()
+        core.set_param("algo", 2)
+        for a, b in pairs:
+            mu, mv = core.compute(a, b)
+            wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), ("gcc+", a, b)
+    core.close()
