@@ -68,7 +68,7 @@ typedef struct {
     int64_t peels;           /* single peels run (a batch counts each chain step)             */
     int64_t candidates;      /* sum of |P|: vertices meeting their bound on full degree        */
     int64_t init_vertices;   /* candidates whose live-candidate count was set                  */
-    int64_t search_probes;   /* adjacency words read while searching candidate boundaries      */
+    int64_t search_probes;   /* 32-byte adjacency sectors read while searching candidate rows  */
     int64_t stream_entries;  /* adjacency entries streamed from the initial violators' rows    */
     int64_t entries;         /* adjacency entries read by the cascade                          */
     int64_t decrements;      /* atomic count decrements, all kernels                           */
@@ -257,7 +257,11 @@ int abcore_serve_stop(abcore_ctx *ctx);
 /* Accumulated counters (see abcore_stats) and the context's device memory. */
 int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
 
-/* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown. */
+/* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown.
+ * Among them: "timing" (1: CUDA events around the launches, summed into abcore_stats.kernel_ms),
+ * "timing_kinds" (single peel: bit ABCORE_K_* set for each kernel kind timed; default 0xff --
+ * an event between two kernels costs the step about as much as a launch), "pdl" (1, default:
+ * the single peel's kernels after the count init launch as programmatic dependents). */
 int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
 
 /* Throughput of random 32-bit atomicSub on this device, per second, with the old value returned

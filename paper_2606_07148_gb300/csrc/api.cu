@@ -443,6 +443,10 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         ABC_TRY(abcore_sync(ctx));
         p.packed_counts = (int)value;
         free_batch(ctx);
+    } else if (k == "pdl") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "pdl must be 0 or 1");
+        ABC_TRY(abcore_sync(ctx));
+        p.pdl = (int)value;
     } else if (k == "round0") {
         if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "round0 must be 0 or 1");
         ABC_TRY(abcore_sync(ctx));
@@ -485,6 +489,10 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "timing must be 0 or 1");
         ABC_TRY(abcore_sync(ctx));
         p.timing = (int)value;
+    } else if (k == "timing_kinds") {
+        if (value < 0 || value > 0xff) return ctx->fail(ABCORE_EINVAL, "timing_kinds must be in [0, 255]");
+        ABC_TRY(abcore_sync(ctx));
+        p.timing_kinds = (int)value;
     } else if (k == "serve_inserts") {
         if (value < 1 || value > (1 << 29)) return ctx->fail(ABCORE_EINVAL, "serve_inserts must be in [1, 2^29]");
         p.serve_inserts = value;
@@ -516,6 +524,7 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "flush_steps") *value = p.flush_steps;
     else if (k == "packed_counts") *value = p.packed_counts;
     else if (k == "round0") *value = p.round0;
+    else if (k == "pdl") *value = p.pdl;
     else if (k == "blocks_per_sm") *value = p.blocks_per_sm;
     else if (k == "mode") *value = p.mode;
     else if (k == "timeout_ms") *value = p.timeout_ms;
@@ -524,6 +533,7 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "batch_wave") *value = p.batch_wave;
     else if (k == "hub_degree") *value = p.hub_degree;
     else if (k == "timing") *value = p.timing;
+    else if (k == "timing_kinds") *value = p.timing_kinds;
     else if (k == "serve_inserts") *value = p.serve_inserts;
     else if (k == "algo") *value = p.algo;
     else return ctx->fail(ABCORE_EINVAL, "unknown parameter '%s'", name);

@@ -16,6 +16,14 @@ __device__ __forceinline__ uint64_t now_ns() {
     return t;
 }
 
+// Programmatic dependent launch. A kernel launched with programmatic stream serialization may be
+// scheduled while the kernel before it on the stream is still running; grid_dep_wait blocks until
+// that grid has completed and its memory operations are visible, so a kernel calls it before it
+// touches global memory. grid_dep_launch lets the next such kernel start launching blocks (they
+// then wait in grid_dep_wait). Both do nothing for a normally serialized launch.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -42,6 +42,9 @@ enum {
 };
 
 // Everything a peel kernel needs, passed by value.
+// marks a U row in the second half of a round0 list entry (the row length is below 2^31)
+constexpr long long L0_UPPER = 1ll << 62;
+
 struct PeelArgs {
     const int64_t *off;      // [n+1] row offsets, internal unified ids
     const int32_t *adj;      // [2m] neighbours, each row ascending
@@ -80,8 +83,9 @@ struct PeelArgs {
     // round0: the count init lists its violators in l0 (not the queue); k_round0 walks their rows
     // with atomics that return nothing, and the scan then queues every other candidate below its
     // bound (see peel.cu)
+    // (an entry is {first adjacency index, row length | L0_UPPER for a U row})
     int32_t round0;
-    int32_t *l0;
+    longlong2 *l0;
     unsigned long long *removed;  // if set, counts the vertices queued
     // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
     // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
@@ -102,6 +106,9 @@ struct Params {
                                // throughput (1.5B edges, (64,64): 2.01 -> 1.74 ms); costs where it is
                                // latency-bound (80M edges, (50,50): 0.30 -> 0.53 ms). The autotuner
                                // decides per workload.
+    int pdl = 1;               // single peel: launch the kernels after the count init as
+                               // programmatic dependents of the one before (each waits for its
+                               // predecessor on the device; the launch latency overlaps its tail)
     int grab_div = 0;          // 0 = automatic (resident warps / 8)
     int threads = 256;
     int blocks_per_sm = 0;     // 0 = occupancy calculator
@@ -113,6 +120,9 @@ struct Params {
                                // 4 measured best on a 500M-edge graph (counts stay closer to L2)
     int debug_stall_slots = 0; // test hook: queue slots reserved but never written
     int timing = 0;            // 1: CUDA events around each launch, summed into stats.kernel_ms
+    int timing_kinds = 0xff;   // single peel: the kernel kinds (bit ABCORE_K_*) timed. An event
+                               // between two kernels costs the step about as much as a launch, so
+                               // a measurement may time only the kind it reports.
     int64_t serve_inserts = 1 << 20;  // inserted edges each served target can hold (ENOMEM beyond)
     int algo = 0;              // abcore_compute: 0 GCC+ when core numbers are prepared and it has
                                // fewer vertices to peel, else GCC; 1 always GCC; 2 always GCC+
@@ -144,6 +154,7 @@ struct SlotInfo {
     int64_t cands = 0, n = 0;
     int emit = 0;
     bool timed = false, has_init = false, has_stream = false;
+    unsigned kinds = 0;  // kernel kinds timed (bit ABCORE_K_*) when timed
 };
 
 struct PeelWork {
@@ -162,7 +173,7 @@ struct PeelWork {
     bool q_dirty = false;          // queue not known to be all-empty
     uint32_t *flags = nullptr;     // [grid * 32] per-block queue-closed flags (epochs)
     int flag_blocks = 0;
-    int32_t *l0 = nullptr;         // [n] initial candidate violators (round0)
+    longlong2 *l0 = nullptr;       // [n] initial candidate violators' rows (round0)
     uint32_t epoch = 0;            // last cascade epoch handed out
 };
 

@@ -36,8 +36,9 @@ using abc::WarpSmem;
 constexpr int INIT_THREADS = 256;
 constexpr int STREAM_THREADS = 256;
 
-__global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
+__global__ void __launch_bounds__(INIT_THREADS, 5) k_init(PeelArgs a) {
     __shared__ abc::PushBuf<64> pbuf[INIT_THREADS / 32];
+    abc::grid_dep_launch();
     LaneStats ls;
     unsigned long long probes = 0, inits = 0;
     abc::init_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls,
@@ -54,6 +55,8 @@ __global__ void __launch_bounds__(INIT_THREADS) k_init(PeelArgs a) {
 
 __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t sa, int64_t ea, int64_t sb,
                                                            int64_t eb) {
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
     LaneStats ls;
     unsigned long long ents = 0;
     abc::stream_range(a, sa, ea, sb, eb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
@@ -70,6 +73,8 @@ __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t s
 
 __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
     __shared__ abc::PushBuf<64> pbuf[256 / 32];
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
     LaneStats ls;
     unsigned long long scanned = 0;
     abc::scan_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls, scanned);
@@ -81,11 +86,16 @@ __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
     }
 }
 
-// round0: the rows of the candidates the count init found below their bound (listed in l0) --
-// the first peel round of Algorithm 1 for them -- walked with decrements that return nothing, as
-// the violator stream does; no crossing is looked for here, k_scan finds every candidate the
-// round took below its bound. Lane l of a warp takes listed vertex base + l and the warp balances
-// their rows' entries over its lanes.
+// round0: the rows of the candidates the count init found below their bound (listed in l0 with
+// their first adjacency index and length) -- the first peel round of Algorithm 1 for them --
+// walked with decrements that return nothing, as the violator stream does; no crossing is looked
+// for here, k_scan finds every candidate the round took below its bound. Lane l of a warp takes
+// list entry base + l and the warp balances their rows' entries over its lanes; the next group's
+// entries are loaded while this group's rows are walked.
+// (Its entries per lane per step, R0_ILP, are twice the cascade's: nothing waits on the atomics,
+// so only the adjacency loads' latency has to be covered.)
+constexpr int R0_ILP = 8;
+
 __global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
     __shared__ long long s_start[256 / 32][32];
     __shared__ int s_excl[256 / 32][32];
@@ -93,29 +103,29 @@ __global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
     const int64_t nl0 = (int64_t)a.ctl->l0n;  // written by k_init, earlier on the stream
     unsigned long long ents = 0, decs = 0;
+    longlong2 nxt = make_longlong2(0, 0);
+    if (gw * 32 + lane < nl0) nxt = __ldg(&a.l0[gw * 32 + lane]);
     for (int64_t g0 = gw * 32; g0 < nl0; g0 += nw * 32) {
-        int32_t x = -1;
-        int len = 0;
-        long long start = 0;
-        if (g0 + lane < nl0) {
-            x = __ldg(&a.l0[g0 + lane]);
-            len = __ldcg(&a.plen[x]);
-            start = __ldg(&a.off[x]);
-        }
+        const longlong2 cur = nxt;  // {0, 0} past the end: an empty row
+        const int64_t g1 = g0 + nw * 32 + lane;
+        if (g1 < nl0) nxt = __ldg(&a.l0[g1]);
+        const int len = (int)(cur.y & 0x7fffffff);
         const int incl = abc::warp_incl_scan(len);
         const int L = __shfl_sync(ABC_FULL, incl, 31);
-        s_start[wib][lane] = start;
+        s_start[wib][lane] = cur.x;
         s_excl[wib][lane] = incl - len;
-        s_upper[wib][lane] = x >= 0 && x < a.nU;
+        s_upper[wib][lane] = (cur.y & L0_UPPER) != 0;
         __syncwarp();
         int j = 0;
-        for (int b = 0; b < L; b += 32 * abc::ILP) {
-            int32_t y[abc::ILP];
-            int up[abc::ILP];
+        for (int b = 0; b < L; b += 32 * R0_ILP) {
+            int32_t y[R0_ILP];
+            int up[R0_ILP];
 #pragma unroll
-            for (int u = 0; u < abc::ILP; ++u) {
+            for (int u = 0; u < R0_ILP; ++u) {
                 const int e = b + 32 * u + lane;
                 y[u] = -1;
                 up[u] = 0;
@@ -126,7 +136,7 @@ __global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < abc::ILP; ++u) {
+            for (int u = 0; u < R0_ILP; ++u) {
                 if (y[u] < 0) continue;
                 ents++;
                 int32_t t;
@@ -156,6 +166,7 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    abc::grid_dep_wait();
     LaneStats ls;
     const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div, blockIdx.x == 0 && wib == 0);
     abc::flush_stats(a, ls);
@@ -223,11 +234,15 @@ int peel_prepare(abcore_ctx *ctx) {
     // every vertex is queued at most once, as ceil(row / chunk) items; idle warps may also hold
     // one ticket batch each beyond the last item
     const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 + (int64_t)ctx->num_sms * 64 * 32;
-    if (w.n == n && w.qcap >= qcap && w.cnt && w.flag_blocks >= cascade_grid(ctx)) return ABCORE_OK;
+    if (w.n == n && w.qcap >= qcap && w.cnt && w.flag_blocks >= cascade_grid(ctx)) {
+        // the round0 list (16 bytes a vertex) is only made once round0 is asked for
+        if (ctx->prm.round0 && !w.l0) ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
+        return ABCORE_OK;
+    }
     free_peel(ctx);
     ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(n, 1), "peel counts"));
     ABC_TRY(ctx->alloc(&w.plen, (size_t)std::max<int64_t>(n, 1), "peel prefixes"));
-    ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
+    if (ctx->prm.round0) ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
@@ -270,11 +285,31 @@ void free_peel(abcore_ctx *ctx) {
     w.n = w.qcap = 0;
 }
 
+// Launch k on the context's stream; with `pdl`, as a programmatic dependent of the kernel before
+// it on the stream (k calls grid_dep_wait before it touches memory).
+template <typename... P, typename... A>
+cudaError_t launch_k(bool pdl, void (*k)(P...), int64_t grid, int block, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max<int64_t>(grid, 1));
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Cost model: per layer, count by searching the candidates' rows, or by streaming the rows of
 // the other layer's initial violators? Both reach the same counts. Costs are in units of one
 // random 32-byte sector read (a search probe), calibrated by measurement on this GPU: a streamed
 // adjacency entry ~0.08, a stream decrement (atomic without return, L2-resident) ~0.8, a
-// candidate's count init ~0.5. Hubs (degree >= hub_degree) count by search in both cases.
+// candidate's count init ~0.5. Hubs (degree >= hub_degree) count by search in both cases. A row
+// search starts where the layer's share f of candidate entries puts the boundary; with the
+// binomial spread sigma = sqrt(L f (1 - f)) of a row of length L about that guess, it reads
+// about 1 + 2 log2(1 + sigma / 8) sectors (one, then a gallop and a bisection over the spread).
 int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, int32_t pV) {
     const Graph &g = ctx->g;
     if (ctx->prm.mode >= 0) return ctx->prm.mode & 3;
@@ -282,20 +317,22 @@ int pick_mode(const abcore_ctx *ctx, int32_t alpha, int32_t beta, int32_t pU, in
     const double pb = ctx->prm.probe_bytes / 32.0;  // relative probe cost (default 1)
     const int hd = ctx->prm.hub_degree > 0 ? ctx->prm.hub_degree : INT32_MAX;
     auto layer = [&](int64_t p, int32_t thr, const std::vector<int64_t> &cnt, const std::vector<int64_t> &edges,
-                     double other_violator_entries) {
+                     double other_violator_entries, double f) {
         // non-hub candidates: degree in [thr, hd)
         const int32_t top = std::max(thr, hd);
         const double pn = (double)(p - std::min<int64_t>(p, cnt_ge(cnt, top)));
         const double en = (double)(cnt_ge(edges, thr) - cnt_ge(edges, top));
         const double avg = pn > 0 ? en / pn : 1.0;
-        const double search = pn * (0.5 + pb * (1.0 + std::log2(std::max(avg, 1.0))));
+        const double sigma = std::sqrt(std::max(avg, 1.0) * f * (1.0 - f));
+        const double search = pn * (0.5 + pb * (1.0 + 2.0 * std::log2(1.0 + sigma / 8.0)));
         // stream: every violator entry is read; the share landing on non-hub candidates decrements
         const double stream = pn * 0.7 + other_violator_entries * (0.08 + 0.8 * (en / m));
         return search <= stream;
     };
     const double eU = (double)cnt_ge(g.edgesU_ge, alpha), eV = (double)cnt_ge(g.edgesV_ge, beta);
-    const bool sU = layer(pU, alpha, g.cntU_ge, g.edgesU_ge, m - eV);
-    const bool sV = layer(pV, beta, g.cntV_ge, g.edgesV_ge, m - eU);
+    // a U row's entries are V ids: the share below the bound is the V candidates' degree over m
+    const bool sU = layer(pU, alpha, g.cntU_ge, g.edgesU_ge, m - eV, eV / m);
+    const bool sV = layer(pV, beta, g.cntV_ge, g.edgesV_ge, m - eU, eU / m);
     return (sU ? 1 : 0) | (sV ? 2 : 0);
 }
 
@@ -373,7 +410,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
-    a.round0 = (ctx->prm.round0 && (a.searchU || a.searchV)) ? 1 : 0;
+    a.round0 = (ctx->prm.round0 && w.l0 && (a.searchU || a.searchV)) ? 1 : 0;
     a.l0 = w.l0;
     a.flags = w.flags;
     a.flag_first = 0;
@@ -386,7 +423,13 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     si.cands = pruned ? Pu : P;
     si.n = n;
     si.emit = a.emit;
-    si.timed = ctx->prm.timing != 0;
+    si.kinds = (unsigned)ctx->prm.timing_kinds & ((1u << ABCORE_K_INIT) | (1u << ABCORE_K_STREAM) | (1u << ABCORE_K_CASCADE));
+    si.timed = ctx->prm.timing != 0 && si.kinds != 0;
+    // events: 0 before the count init, 1 after it, 2 before the cascade, 3 after it; only those
+    // bounding a timed kind are recorded
+    const bool t_init = si.timed && (si.kinds & (1u << ABCORE_K_INIT));
+    const bool t_first = si.timed && (si.kinds & (1u << ABCORE_K_STREAM));
+    const bool t_casc = si.timed && (si.kinds & (1u << ABCORE_K_CASCADE));
     if (si.timed)
         for (int k = 0; k < 4; ++k)
             if (!w.ev[slot][k]) ABC_CU(cudaEventCreate(&w.ev[slot][k]));
@@ -399,7 +442,11 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         if (nU) ABC_CU(cudaMemsetAsync(d_mask_u, 0, (size_t)nU, ctx->stream));
         if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
     }
-    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
+    if (t_init) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
+    // the kernels after the count init follow it as programmatic dependents, except right after
+    // a timing event (which must see the kernel before it end)
+    const bool pdl = ctx->prm.pdl != 0;
+    bool prev_k = false;  // the last operation on the stream is one of these kernels
     if (Pu > 0) {
         // at most the blocks that fit at once: each lane then walks several candidates
         if (ctx->init_blocks <= 0) {
@@ -409,9 +456,13 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         }
         const int64_t gi = std::min<int64_t>((Pu + INIT_THREADS - 1) / INIT_THREADS, ctx->init_blocks);
         k_init<<<(unsigned)std::max<int64_t>(gi, 1), INIT_THREADS, 0, ctx->stream>>>(a);
+        prev_k = true;
         si.has_init = true;
         ctx->stats.launches++;
-        if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][1], ctx->stream));
+        if (t_init || t_first) {
+            ABC_CU(cudaEventRecord(w.ev[slot][1], ctx->stream));
+            prev_k = false;
+        }
         // Rows of the initial violators are contiguous: U violators [pU, nU) own
         // adj[off[pU], off[nU]) = [edgesU_ge(alpha), m), V violators [nU+pV, n) own
         // adj[m + edgesV_ge(beta), 2m). Slice A (V rows) feeds U counts, slice B (U rows) V counts.
@@ -429,7 +480,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             const int64_t work = ((ea - sa) + (eb - sb)) / 4 + 1;
             const int64_t gs = std::min<int64_t>((work + STREAM_THREADS - 1) / STREAM_THREADS,
                                                  (int64_t)ctx->num_sms * 16);
-            k_stream<<<(unsigned)std::max<int64_t>(gs, 1), STREAM_THREADS, 0, ctx->stream>>>(a, sa, ea, sb, eb);
+            ABC_CU(launch_k(pdl && prev_k, k_stream, gs, STREAM_THREADS, ctx->stream, a, sa, ea, sb, eb));
             si.has_stream = true;
             ctx->stats.launches++;
         }
@@ -437,7 +488,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             // the initial candidate violators' rows (their count is below the bound, so each row
             // is shorter than the bound)
             const int64_t gr = std::min<int64_t>((Pu + 255) / 256, (int64_t)ctx->num_sms * 16);
-            k_round0<<<(unsigned)std::max<int64_t>(gr, 1), 256, 0, ctx->stream>>>(a);
+            ABC_CU(launch_k(pdl && prev_k, k_round0, gr, 256, ctx->stream, a));
             si.has_stream = true;
             ctx->stats.launches++;
         }
@@ -446,15 +497,21 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             const int64_t ns = a.round0 ? Pu
                                         : (a.searchU ? 0 : (int64_t)pU - a.hubcutU) + (a.searchV ? 0 : (int64_t)pV - a.hubcutV);
             const int64_t gsc = std::min<int64_t>((ns + 255) / 256, (int64_t)ctx->num_sms * 16);
-            k_scan<<<(unsigned)std::max<int64_t>(gsc, 1), 256, 0, ctx->stream>>>(a);
+            ABC_CU(launch_k(pdl && prev_k, k_scan, gsc, 256, ctx->stream, a));
             ctx->stats.launches++;
         }
     }
-    if (ctx->prm.debug_stall_slots > 0) k_stall<<<1, 1, 0, ctx->stream>>>(ctl, w.qcap, ctx->prm.debug_stall_slots);
-    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][2], ctx->stream));
-    k_cascade<<<blocks, 256, 0, ctx->stream>>>(a);
+    if (ctx->prm.debug_stall_slots > 0) {
+        k_stall<<<1, 1, 0, ctx->stream>>>(ctl, w.qcap, ctx->prm.debug_stall_slots);
+        prev_k = false;
+    }
+    if (t_first || t_casc) {
+        ABC_CU(cudaEventRecord(w.ev[slot][2], ctx->stream));
+        prev_k = false;
+    }
+    ABC_CU(launch_k(pdl && prev_k, k_cascade, blocks, 256, ctx->stream, a));
     ctx->stats.launches++;
-    if (si.timed) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
+    if (t_casc) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
     ABC_CU(cudaGetLastError());
     ABC_CU(cudaMemcpyAsync(w.ctl_host + slot, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, ctx->stream));
     w.pending[slot] = true;
@@ -499,15 +556,17 @@ int peel_finish(abcore_ctx *ctx) {
         }
         if (si.timed) {
             float ms = 0.f;
-            if (si.has_init && cudaEventElapsedTime(&ms, w.ev[i][0], w.ev[i][1]) == cudaSuccess) {
+            if (si.has_init && (si.kinds & (1u << ABCORE_K_INIT)) &&
+                cudaEventElapsedTime(&ms, w.ev[i][0], w.ev[i][1]) == cudaSuccess) {
                 s.kernel_ms[ABCORE_K_INIT] += ms;
                 s.kernel_launches[ABCORE_K_INIT]++;
             }
-            if (si.has_stream && cudaEventElapsedTime(&ms, w.ev[i][1], w.ev[i][2]) == cudaSuccess) {
+            if (si.has_stream && (si.kinds & (1u << ABCORE_K_STREAM)) &&
+                cudaEventElapsedTime(&ms, w.ev[i][1], w.ev[i][2]) == cudaSuccess) {
                 s.kernel_ms[ABCORE_K_STREAM] += ms;
                 s.kernel_launches[ABCORE_K_STREAM]++;
             }
-            if (cudaEventElapsedTime(&ms, w.ev[i][2], w.ev[i][3]) == cudaSuccess) {
+            if ((si.kinds & (1u << ABCORE_K_CASCADE)) && cudaEventElapsedTime(&ms, w.ev[i][2], w.ev[i][3]) == cudaSuccess) {
                 s.kernel_ms[ABCORE_K_CASCADE] += ms;
                 s.kernel_launches[ABCORE_K_CASCADE]++;
             }

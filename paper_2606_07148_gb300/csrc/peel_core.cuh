@@ -477,6 +477,53 @@ __device__ __forceinline__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl
     return ok != 0;
 }
 
+// Length of the prefix of the sorted row adj[s, e) (s < e) holding ids below `bound`: the row's
+// candidate neighbours. The search reads whole 32-byte sectors (the 8 entries of the aligned
+// sector, clipped to the open range) and starts at s + frac * (e - s), frac being the share of
+// the whole layer's adjacency entries that lie below the bound -- where the boundary of a row
+// whose neighbours are drawn like everyone else's falls. From there it gallops outward in
+// doubling steps until the boundary is bracketed, then bisects. The result does not depend on
+// frac; a good guess settles most rows in one sector where bisection reads log2(length / 8).
+// `probes` counts the sectors read.
+__device__ __forceinline__ int row_prefix(const int32_t *__restrict__ adj, int64_t s, int64_t e, int32_t bound,
+                                          float frac, unsigned long long &probes) {
+    const int32_t *row = adj + s;
+    const int d = (int)(e - s);
+    int lo = 0, hi = d;  // the boundary (first index holding an id >= bound, or d) is in [lo, hi]
+    int p = (int)(frac * (float)d);
+    p = p < 0 ? 0 : (p >= d ? d - 1 : p);
+    const int mis = (int)((reinterpret_cast<uintptr_t>(row) >> 2) & 7);  // entries past a sector start
+    int dist = 8;
+    int dir = 0;  // 0: first probe; +1 / -1: galloping right / left; 2: bracketed, bisecting
+    while (lo < hi) {  // p is in [lo, hi): every pass shrinks the range
+        const int w = ((p + mis) & ~7) - mis;
+        const int w0 = max(w, lo), w1 = min(w + 8, hi);
+        int below = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = w + k;
+            if (i >= w0 && i < w1) below += __ldg(&row[i]) < bound ? 1 : 0;
+        }
+        probes++;
+        if (below > 0 && below < w1 - w0) return w0 + below;
+        const int want = below == 0 ? -1 : 1;
+        if (below == 0) hi = w0;
+        else lo = w1;
+        if (lo >= hi) break;
+        if (dir == 0 || dir == want) {
+            dir = want;
+            // (a row is shorter than 2^31, so w1 - 1 + dist stays in range: dist < 2 * d)
+            p = want > 0 ? w1 - 1 + dist : w0 - dist;
+            dist <<= 1;
+            p = p < lo ? lo : (p >= hi ? hi - 1 : p);
+        } else {
+            dir = 2;
+        }
+        if (dir == 2) p = lo + ((hi - lo) >> 1);
+    }
+    return lo;
+}
+
 // Candidate counts (the scan phase): thread t of nthreads handles candidates t, t + nthreads, ...
 // Per layer, the count is either the row prefix below the other layer's candidate boundary
 // (binary search in the sorted row) or the full degree (to be corrected by stream_range).
@@ -489,6 +536,11 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
     const int64_t nu = (int64_t)a.pU - a.cU, P = nu + (a.pV - a.cV);  // uncertain candidates
     const int lane = threadIdx.x & 31;
     int pc = 0;
+    // the share of U-row entries that are V candidates (the candidates' total degree over m), and
+    // of V-row entries that are U candidates: each row search starts from it
+    const int64_t mU = __ldg(&a.off[a.nU]), mV = __ldg(&a.off[(int64_t)a.nU + a.nV]) - mU;
+    const float fracU = mU > 0 ? (float)(__ldg(&a.off[(int64_t)a.nU + a.pV]) - mU) / (float)mU : 0.f;
+    const float fracV = mV > 0 ? (float)__ldg(&a.off[a.pU]) / (float)mV : 0.f;
     for (int64_t b = t0 - lane; b < P; b += nthreads * INIT_ILP) {
         int32_t x[INIT_ILP];
         int64_t s[INIT_ILP], e[INIT_ILP];
@@ -506,30 +558,14 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
 #pragma unroll
         for (int k = 0; k < INIT_ILP; ++k) {
             bool viol = false;
-            int nch = 0;
+            int nch = 0, len = 0;
+            const bool upper = x[k] >= 0 && x[k] < a.nU;
             if (x[k] >= 0) {
-                const bool upper = x[k] < a.nU;
-                int len;
                 const bool hubx = upper ? x[k] < a.hubcutU : x[k] - a.nU < a.hubcutV;
                 if ((upper ? a.searchU : a.searchV) || hubx) {
                     // candidate neighbours form the row's prefix below the other layer's bound
                     const int32_t bound = upper ? a.nU + a.pV : a.pU;
-                    if (e[k] == s[k]) {
-                        len = 0;
-                    } else if (__ldg(&a.adj[e[k] - 1]) < bound) {
-                        len = (int)(e[k] - s[k]);
-                        probes++;
-                    } else {
-                        int64_t lo = s[k], hi = e[k] - 1;  // adj[hi] >= bound
-                        probes++;
-                        while (lo < hi) {
-                            const int64_t mid = (lo + hi) >> 1;
-                            probes++;
-                            if (__ldg(&a.adj[mid]) < bound) lo = mid + 1;
-                            else hi = mid;
-                        }
-                        len = (int)(lo - s[k]);
-                    }
+                    len = e[k] == s[k] ? 0 : row_prefix(a.adj, s[k], e[k], bound, upper ? fracU : fracV, probes);
                 } else {
                     len = (int)(e[k] - s[k]);
                 }
@@ -547,7 +583,8 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                     if (lane == 0) base = atomicAdd(&a.ctl->l0n, (unsigned long long)__popc(vm));
                     base = __shfl_sync(ABC_FULL, base, 0);
                     if (viol) {
-                        a.l0[base + __popc(vm & lanemask_lt())] = x[k];
+                        // the row's first entry, length and layer: k_round0 needs nothing more
+                        a.l0[base + __popc(vm & lanemask_lt())] = make_longlong2(s[k], (long long)len | (upper ? L0_UPPER : 0));
                         ls.pushes++;
                     }
                 }

@@ -94,14 +94,14 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
     if (!rc) rc = ctx->alloc(&T.flush, T.flush_bytes, "L2 flush buffer");
     if (!rc && (cudaEventCreate(&T.e0) != cudaSuccess || cudaEventCreate(&T.e1) != cudaSuccess))
         rc = ctx->fail(ABCORE_ECUDA, "autotune: event creation failed");
-    const int reps = 3;
+    const int reps = 5;
     double best = -1;
     if (!rc) {
         best = time_sample(ctx, T, batch, n, alphas, betas, mu, mv, reps);
         if (best < 0) rc = ctx->err.empty() ? ctx->fail(ABCORE_ECUDA, "autotune: a timed run failed") : ABCORE_ECUDA;
     }
-    // coordinate descent, two sweeps
-    for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
+    // coordinate descent, up to three sweeps
+    for (int sweep = 0; sweep < 3 && !rc; ++sweep) {
         bool moved = false;
         for (const Knob &k : knobs) {
             int64_t cur = 0;
@@ -117,7 +117,7 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
                 }
                 // a margin keeps timing noise from moving settings (a batch of chains varies
                 // more from run to run than a single peel)
-                if (t < best * (batch ? 0.95 : 0.98)) {
+                if (t < best * (batch ? 0.95 : 0.985)) {
                     best = t;
                     keep = v;
                     moved = true;

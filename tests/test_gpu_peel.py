@@ -293,3 +293,86 @@ def test_round0_first_round_without_returns(mode):
             wu, wv = oracle.peel(nU, nV, off, adj, a, b)
             assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), ("gcc+", a, b)
     core.close()
+
+
+def _hub_graph(seed):
+    # a few U hubs adjacent to most of V plus a sparse random part: long sorted rows whose
+    # candidate boundary sits anywhere, including far from the layer-wide share
+    rng = np.random.default_rng(seed)
+    nU, nV = 3000, 2500
+    hubs = 5
+    eu = [np.full(nV - 100 * h, h) for h in range(hubs)]
+    ev = [np.arange(100 * h, nV) for h in range(hubs)]
+    m_rand = 30000
+    eu.append(rng.integers(hubs, nU, m_rand))
+    ev.append(rng.integers(0, nV, m_rand))
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    key = np.unique(eu.astype(np.int64) * nV + ev)
+    return nU, nV, (key // nV).astype(np.int32), (key % nV).astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_row_search_on_long_skewed_rows(seed):
+    # every count by search (mode 3) over hub rows of 2000+ entries and short random rows, for
+    # thresholds that move each layer's candidate boundary from a few ids to most of the layer
+    nU, nV, eu, ev = _hub_graph(seed)
+    off, adj = oracle.build_csr(nU, nV, eu, ev)
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    core.set_param("mode", 3)
+    for a, b in [(1, 1), (2, 2), (5, 1), (1, 6), (9, 3), (12, 12), (30, 2), (2, 40)]:
+        mu, mv = core.compute(a, b)
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (a, b)
+    core.close()
+
+
+@pytest.mark.parametrize("pdl", [0, 1])
+def test_dependent_launches_back_to_back(pdl):
+    # the kernels after the count init launched as programmatic dependents (or not): many
+    # asynchronous peels in a row, in every counting mode and with round0, equal the oracle's
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.set_param("pdl", pdl)
+    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8)]
+    want = {p: oracle.peel(nU, nV, off, adj, *p) for p in pairs}
+    for mode in (0, 1, 2, 3):
+        for r0 in (0, 1):
+            core.set_param("mode", mode)
+            core.set_param("round0", r0)
+            outs = []
+            for a, b in pairs * 3:
+                mu = torch.zeros(nU, dtype=torch.uint8, device="cuda")
+                mv = torch.zeros(nV, dtype=torch.uint8, device="cuda")
+                core.compute(a, b, mu, mv, asynchronous=True)
+                outs.append(((a, b), mu, mv))
+            core.sync()
+            for p, mu, mv in outs:
+                wu, wv = want[p]
+                assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (pdl, mode, r0, p)
+    core.close()
+
+
+def test_timing_kinds_selects_the_timed_launches():
+    # events around the chosen kernel kinds only; the cores do not change
+    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.set_param("mode", 3)  # every count by search: init, then the cascade
+    wu, wv = oracle.peel(nU, nV, off, adj, 3, 3)
+    for kinds, timed in [(0xFF, (1, 0, 1)), (1 << abi.K_CASCADE, (0, 0, 1)), (1 << abi.K_INIT, (1, 0, 0))]:
+        core.set_param("timing", 1)
+        core.set_param("timing_kinds", kinds)
+        core.set_param("reset_stats", 1)
+        mu, mv = core.compute(3, 3)
+        core.sync()
+        st = core.stats()
+        assert tuple(st["kernel_launches"][:3]) == timed, kinds
+        assert (st["kernel_ms"][abi.K_CASCADE] > 0) == bool(timed[2])
+        assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv)
+    with pytest.raises(ABCoreError):
+        core.set_param("timing_kinds", 256)
+    core.close()
