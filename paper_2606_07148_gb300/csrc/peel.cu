@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
     for (int64_t g0 = gw * 32; g0 < nl0; g0 += nw * 32) {
         const longlong2 cur = nxt;  // {0, 0} past the end: an empty row
         const int64_t g1 = g0 + nw * 32 + lane;
-        if (g1 < nl0) nxt = __ldg(&a.l0[g1]);
+        nxt = g1 < nl0 ? __ldg(&a.l0[g1]) : make_longlong2(0, 0);
         const int len = (int)(cur.y & 0x7fffffff);
         const int incl = abc::warp_incl_scan(len);
         const int L = __shfl_sync(ABC_FULL, incl, 31);

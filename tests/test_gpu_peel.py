@@ -376,3 +376,34 @@ def test_timing_kinds_selects_the_timed_launches():
     with pytest.raises(ABCoreError):
         core.set_param("timing_kinds", 256)
     core.close()
+
+
+def test_round0_violator_list_longer_than_the_grid():
+    # k_round0's grid is capped (16 blocks of 256 lanes per SM), so each warp walks several
+    # groups of the violator list when it holds more entries than the grid has lanes; every
+    # lane past the list's end must walk nothing. 4M x 4M vertices, 16M edges, light-tailed
+    # degrees: (4,4) with every count by search leaves ~1.4M initial candidate violators.
+    spec = dict(nU=4_000_000, nV=4_000_000, m=16_000_000, gamma_u=4.0, gamma_v=4.0, seed=7, kmax=None)
+    nU, nV, eu, ev = synth.make_graph(spec)
+    eu, ev = eu.numpy(), ev.numpy()
+    off, adj = oracle.build_csr(nU, nV, eu, ev)
+    lanes = torch.cuda.get_device_properties(0).multi_processor_count * 16 * 256
+    deg = np.diff(off)
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    core.set_param("mode", 3)
+    for a, b in [(4, 4), (3, 5), (3, 3)]:
+        thr = np.concatenate([np.full(nU, a), np.full(nV, b)])
+        cand = deg >= thr
+        # live-candidate count of each candidate: its neighbours that are candidates
+        csum = np.concatenate([[0], np.cumsum(cand[adj], dtype=np.int64)])
+        nb_cand = csum[off[1:]] - csum[off[:-1]]
+        n_viol = int((cand & (nb_cand < thr)).sum())
+        if (a, b) == (4, 4):
+            assert n_viol > 2 * lanes, (n_viol, lanes)  # several groups per warp
+        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+        for r0 in (0, 1):
+            core.set_param("round0", r0)
+            mu, mv = core.compute(a, b)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (a, b, r0)
+    core.close()
