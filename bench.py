@@ -166,11 +166,13 @@ def algorithmic_bytes(st):
     # cascade: per item 8 B queue read + 8 B slot reset + 8 B offset + 4 B row length;
     # per entry 4 B; per decrement 8 B; per push 8 B queue write (the row length is read by
     # the consumer, inside the item's figure);
-    # emission: gather 4 B old2new + 1 B mask per vertex, plus 4 B count per candidate; scatter
-    # 4 B count per candidate
+    # emission: a gather reads 4 B old2new and 1/8 B of the removed-candidate bitmap (and clears
+    # it: 1/8 B) and writes 1 B of mask per vertex, and every removal sets its bit (4 B new2old
+    # + 4 B bitmap word); a scatter reads 4 B count per candidate
     dec_casc = st["decrements"] - dec_stream
+    marks = 8 * st["pushes"] if st["emit_gathered"] > 0 else 0
     b[2] = (28 * st["items"] + 4 * st["entries"] + 8 * dec_casc + 8 * st["pushes"]
-            + 5 * st["emit_gathered"] + 4 * st["candidates"])
+            + 5.25 * st["emit_gathered"] + marks + 4 * st["emit_scattered"])
     return b
 
 

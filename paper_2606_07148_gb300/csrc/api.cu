@@ -470,6 +470,9 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
     } else if (k == "timeout_ms") {
         if (value < 1) return ctx->fail(ABCORE_EINVAL, "timeout_ms must be >= 1");
         p.timeout_ms = value;
+    } else if (k == "emit_bitmap_min_pct") {
+        if (value < 0 || value > 101) return ctx->fail(ABCORE_EINVAL, "emit_bitmap_min_pct must be 0..101");
+        p.emit_bitmap_min_pct = (int)value;
     } else if (k == "emit_scatter_max_pct") {
         if (value < 0 || value > 100) return ctx->fail(ABCORE_EINVAL, "emit_scatter_max_pct must be 0..100");
         p.emit_scatter_max_pct = (int)value;
@@ -529,6 +532,7 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "mode") *value = p.mode;
     else if (k == "timeout_ms") *value = p.timeout_ms;
     else if (k == "emit_scatter_max_pct") *value = p.emit_scatter_max_pct;
+    else if (k == "emit_bitmap_min_pct") *value = p.emit_bitmap_min_pct;
     else if (k == "probe_bytes") *value = (int64_t)p.probe_bytes;
     else if (k == "batch_wave") *value = p.batch_wave;
     else if (k == "hub_degree") *value = p.hub_degree;

@@ -87,6 +87,10 @@ struct PeelArgs {
     int32_t round0;
     longlong2 *l0;
     unsigned long long *removed;  // if set, counts the vertices queued
+    // if set: a bitmap over caller ids (bit layer base + caller id) of the candidates this peel
+    // removes, set when the cascade takes a fallen vertex's first chunk (round0: when the count
+    // init lists it) and read, then cleared, by the caller-order mask gather
+    uint32_t *fallen;
     // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
     // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
     uint32_t *flags;
@@ -115,6 +119,8 @@ struct Params {
     int mode = -1;             // -1 auto; else bit 0 searchU, bit 1 searchV
     long long timeout_ms = 4000;
     int emit_scatter_max_pct = 5;  // scatter masks when |P| <= this % of n
+    int emit_bitmap_min_pct = 0;   // gather: test removal in the caller-order bitmap when |P| >= this
+                                   // % of n (each removal then sets its bit), else read the count
     double probe_bytes = 32.0;     // cost model: bytes charged per search probe
     int batch_wave = 4;        // chains sharing the GPU at once (0 = as many as fit, up to 32);
                                // 4 measured best on a 500M-edge graph (counts stay closer to L2)
@@ -174,6 +180,8 @@ struct PeelWork {
     uint32_t *flags = nullptr;     // [grid * 32] per-block queue-closed flags (epochs)
     int flag_blocks = 0;
     longlong2 *l0 = nullptr;       // [n] initial candidate violators' rows (round0)
+    uint32_t *fallen = nullptr;    // [(n + 31) / 32] removed-candidate bitmap (all zero between peels)
+    bool fallen_dirty = false;     // a failed peel may have left bits set
     uint32_t epoch = 0;            // last cascade epoch handed out
 };
 

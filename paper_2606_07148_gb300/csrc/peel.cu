@@ -173,27 +173,90 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
     if (!ok || a.emit == 0) return;
     const int64_t n = (int64_t)a.nU + a.nV;
     if (a.emit == 1) {
-        // gather in the caller's order: every count is final once the queue has closed. Each
-        // lane keeps EMIT_ILP independent id -> count -> mask chains in flight (this grid is
-        // small: one lane per chain would wait out every round trip in turn).
-        constexpr int EMIT_ILP = 8;
+        // gather in the caller's order, once the queue has closed: caller id i is in the core
+        // iff its internal id y = old2new[i] is a candidate that the peel did not remove. With
+        // the bitmap (a.fallen), removal is bit i, set when the vertex fell; every load is then
+        // coalesced, and the warp that reads a word clears it for the next peel (a word's ids
+        // always fall to one warp). Without it, removal is read from y's count (one random
+        // read per candidate). Lanes take four consecutive caller ids each (16-byte id loads,
+        // 4-byte mask stores) when the masks' alignment allows, else one.
+        const bool vec = ((reinterpret_cast<uintptr_t>(a.mask_u) | reinterpret_cast<uintptr_t>(a.mask_v)) & 3) == 0 &&
+                         (a.nU & 3) == 0;
         const int64_t stride = nw * 32;
-        for (int64_t i0 = gw * 32 + lane; i0 < n; i0 += stride * EMIT_ILP) {
-            int32_t x[EMIT_ILP];
+        if (vec) {
+            constexpr int QILP = 4;  // quads in flight per lane
+            const int64_t nq = (n + 3) >> 2;
+            const int4 *o4 = reinterpret_cast<const int4 *>(a.old2new);
+            for (int64_t q0 = gw * 32 + lane; q0 - lane < nq; q0 += stride * QILP) {
+                int4 xv[QILP];
+                uint32_t f[QILP];
 #pragma unroll
-            for (int k = 0; k < EMIT_ILP; ++k) {
-                const int64_t i = i0 + k * stride;
-                x[k] = i < n ? __ldg(&a.old2new[i]) : 0;
+                for (int k = 0; k < QILP; ++k) {
+                    const int64_t q = q0 + k * stride;
+                    xv[k] = make_int4(0, 0, 0, 0);
+                    if (4 * q + 3 < n) {
+                        xv[k] = __ldg(&o4[q]);
+                    } else if (4 * q < n) {  // the last, partial quad
+                        xv[k].x = __ldg(&a.old2new[4 * q]);
+                        if (4 * q + 1 < n) xv[k].y = __ldg(&a.old2new[4 * q + 1]);
+                        if (4 * q + 2 < n) xv[k].z = __ldg(&a.old2new[4 * q + 2]);
+                    }
+                    f[k] = (a.fallen != nullptr && q < nq) ? __ldcg(&a.fallen[q >> 3]) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < QILP; ++k) {
+                    const int64_t q = q0 + k * stride;
+                    if (q >= nq) continue;
+                    const int32_t ys[4] = {xv[k].x, xv[k].y, xv[k].z, xv[k].w};
+                    uint32_t bytes = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        bool in;
+                        if (a.fallen != nullptr) {
+                            const int32_t y = ys[j];
+                            in = (y < a.nU ? y < a.pU : y - a.nU < a.pV) &&
+                                 ((f[k] >> (((unsigned)q & 7u) * 4u + (unsigned)j)) & 1u) == 0;
+                        } else {
+                            in = 4 * q + j < n && alive_of(a, ys[j]);
+                        }
+                        bytes |= (in ? 1u : 0u) << (8 * j);
+                    }
+                    const int64_t i = q * 4;
+                    uint8_t *dst = i < a.nU ? a.mask_u + i : a.mask_v + (i - a.nU);
+                    if (i + 3 < n) {
+                        *reinterpret_cast<uint32_t *>(dst) = bytes;
+                    } else {
+                        for (int j = 0; i + j < n; ++j) dst[j] = (uint8_t)(bytes >> (8 * j));
+                    }
+                }
+                if (a.fallen != nullptr) {
+                    // the eight lanes sharing a bitmap word have read it: the first one clears it
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < QILP; ++k) {
+                        const int64_t q = q0 + k * stride;
+                        if (q < nq && (q & 7) == 0 && f[k] != 0u) a.fallen[q >> 3] = 0u;
+                    }
+                }
             }
-            uint8_t v[EMIT_ILP];
-#pragma unroll
-            for (int k = 0; k < EMIT_ILP; ++k) v[k] = (i0 + k * stride < n && alive_of(a, x[k])) ? 1 : 0;
-#pragma unroll
-            for (int k = 0; k < EMIT_ILP; ++k) {
-                const int64_t i = i0 + k * stride;
-                if (i >= n) break;
-                if (i < a.nU) a.mask_u[i] = v[k];
-                else a.mask_v[i - a.nU] = v[k];
+        } else {
+            for (int64_t i0 = gw * 32 + lane; i0 - lane < n; i0 += stride) {
+                const int64_t i = i0;
+                const int32_t y = i < n ? __ldg(&a.old2new[i]) : 0;
+                const uint32_t word = (a.fallen != nullptr && i < n) ? __ldcg(&a.fallen[i >> 5]) : 0u;
+                if (i < n) {
+                    bool in;
+                    if (a.fallen != nullptr)
+                        in = (y < a.nU ? y < a.pU : y - a.nU < a.pV) && ((word >> (i & 31)) & 1u) == 0;
+                    else
+                        in = alive_of(a, y);
+                    if (i < a.nU) a.mask_u[i] = in ? 1 : 0;
+                    else a.mask_v[i - a.nU] = in ? 1 : 0;
+                }
+                if (a.fallen != nullptr) {
+                    __syncwarp();
+                    if (lane == 0 && i < n && word != 0u) a.fallen[i >> 5] = 0u;
+                }
             }
         }
     } else {
@@ -246,6 +309,9 @@ int peel_prepare(abcore_ctx *ctx) {
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
     ABC_TRY(ctx->alloc(&w.ctl, CTL_RING, "peel control"));
     ABC_TRY(ctx->alloc(&w.stage, (size_t)std::max<int64_t>(n, 1), "mask staging"));
+    ABC_TRY(ctx->alloc(&w.fallen, (size_t)((n + 31) / 32 + 1), "removed-candidate bitmap"));
+    ABC_CU(cudaMemsetAsync(w.fallen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1), ctx->stream));
+    w.fallen_dirty = false;
     w.flag_blocks = cascade_grid(ctx);
     ABC_TRY(ctx->alloc(&w.flags, (size_t)w.flag_blocks * 32, "queue close flags"));
     ABC_CU(cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (size_t)w.flag_blocks * 32, ctx->stream));
@@ -269,6 +335,7 @@ void free_peel(abcore_ctx *ctx) {
     ctx->release(w.q);
     ctx->release(w.ctl);
     ctx->release(w.stage);
+    ctx->release(w.fallen);
     ctx->release(w.flags);
     w.flag_blocks = 0;
     if (w.ctl_host) cudaFreeHost(w.ctl_host);
@@ -410,6 +477,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     const bool scatter = P * 100 <= (int64_t)ctx->prm.emit_scatter_max_pct * n;
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
+    a.fallen = (a.emit == 1 && P * 100 >= (int64_t)ctx->prm.emit_bitmap_min_pct * n) ? w.fallen : nullptr;
     a.round0 = (ctx->prm.round0 && w.l0 && (a.searchU || a.searchV)) ? 1 : 0;
     a.l0 = w.l0;
     a.flags = w.flags;
@@ -438,6 +506,10 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         w.q_dirty = false;
     }
     ABC_CU(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), ctx->stream));
+    if (a.fallen != nullptr && w.fallen_dirty) {
+        ABC_CU(cudaMemsetAsync(w.fallen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1), ctx->stream));
+        w.fallen_dirty = false;
+    }
     if (a.emit == 2) {
         if (nU) ABC_CU(cudaMemsetAsync(d_mask_u, 0, (size_t)nU, ctx->stream));
         if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
@@ -574,6 +646,7 @@ int peel_finish(abcore_ctx *ctx) {
     }
     if (first_err != 0) {
         w.q_dirty = true;
+        w.fallen_dirty = true;
         if (first_err == ABCORE_ETIMEDOUT)
             return ctx->fail(ABCORE_ETIMEDOUT, "peel: a bounded device wait expired (limit %lld ms)",
                              (long long)ctx->prm.timeout_ms);

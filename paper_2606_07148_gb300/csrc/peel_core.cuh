@@ -127,11 +127,19 @@ __device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, 
 // Warp-collective: lanes with `want` queue nch items of vertex y, chunks [c0, c0 + nch); nch == 0
 // queues nothing. With `fallen`, y is a vertex that has just fallen (it is counted, and its
 // removal step recorded). Flushes when the buffer is nearly full.
+// Record removed candidate x (caller id o within its layer) in the caller-order bitmap.
+__device__ __forceinline__ void mark_fallen(const PeelArgs &a, int32_t x, int32_t o) {
+    const uint32_t u = (uint32_t)(x < a.nU ? o : a.nU + o);
+    atomicOr(&a.fallen[u >> 5], 1u << (u & 31));
+}
+
 template <int CAP>
 __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, int &pc, bool want, int32_t y, int nch,
                                          LaneStats &ls, bool fallen = true, int c0 = 0) {
     if (want && fallen) {
         ls.pushes++;
+        // a removal with an empty row is never queued, so nothing else would record it
+        if (nch == 0 && a.fallen != nullptr) mark_fallen(a, y, __ldg(&a.new2old[y]));
         if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
         if (a.corev) a.corev[y] = a.step;
     }
@@ -153,6 +161,7 @@ __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, in
 }
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
+
 
 // Entries handled per lane per step by the streaming and cascade loops: the loads, then the
 // atomics, of one step are independent, so they overlap instead of waiting one at a time.
@@ -177,10 +186,11 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
     const int lane = threadIdx.x & 31;
     long long start = 0;
     int len = 0, upper = 0, more = 0, c = 0;
-    int32_t x = 0;
+    int32_t x = 0, o = -1;
     if (it != EMPTY) {
         x = (int32_t)(it >> 32);
         c = (int)(it & 0xffffffffu);
+        if (a.fallen != nullptr && c == 0) o = __ldg(&a.new2old[x]);  // caller id, for the bitmap
         const int rl = row_len_of(a, x);
         start = __ldg(&a.off[x]) + (long long)c * a.chunk;
         len = min(a.chunk, rl - c * a.chunk);
@@ -196,6 +206,7 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
     push_add(a, sm.push, pc, more > 0 && !defer, x, more, ls, /*fallen=*/false, /*c0=*/1);
     if (defer) len = 0;
     if (it != EMPTY && !defer) ls.items++;
+    if (o >= 0 && !defer) mark_fallen(a, x, o);
     push_flush(a, sm.push, pc);
     incl = warp_incl_scan(len);
     const int L = __shfl_sync(ABC_FULL, incl, 31);
@@ -583,6 +594,7 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                     if (lane == 0) base = atomicAdd(&a.ctl->l0n, (unsigned long long)__popc(vm));
                     base = __shfl_sync(ABC_FULL, base, 0);
                     if (viol) {
+                        if (a.fallen != nullptr) mark_fallen(a, x[k], __ldg(&a.new2old[x[k]]));
                         // the row's first entry, length and layer: k_round0 needs nothing more
                         a.l0[base + __popc(vm & lanemask_lt())] = make_longlong2(s[k], (long long)len | (upper ? L0_UPPER : 0));
                         ls.pushes++;
@@ -668,24 +680,37 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
     const int64_t u0 = a.round0 ? a.cU : (a.searchU ? a.pU : max(a.hubcutU, a.cU));
     const int64_t v0 = a.round0 ? a.cV : (a.searchV ? a.pV : max(a.hubcutV, a.cV));
     const int64_t nu = a.pU - u0, total = nu + (a.pV - v0);
-    for (int64_t b = t0 - lane; b < total; b += nthreads) {
-        const int64_t i = b + lane;
-        bool viol = false;
-        int32_t x = 0;
-        int nch = 0;
-        if (i < total) {
-            x = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
-            const int c = cnt_load(a, x);
-            const int thr = x < a.nU ? a.thrU : a.thrV;
-            viol = c < thr;
-            if (viol) {
-                const int pl = __ldcg(&a.plen[x]);
-                if (a.round0 && pl < thr) viol = false;  // an initial violator: round0 walked it
-                else nch = pl > 0 ? 1 : 0;               // chunk 0 (see process_items)
+    // SCAN_ILP candidates per lane per pass, so their count loads are in flight together
+    constexpr int SCAN_ILP = 4;
+    for (int64_t b = t0 - lane; b < total; b += nthreads * SCAN_ILP) {
+        int32_t x[SCAN_ILP];
+        int c[SCAN_ILP];
+#pragma unroll
+        for (int k = 0; k < SCAN_ILP; ++k) {
+            const int64_t i = b + lane + k * nthreads;
+            x[k] = -1;
+            c[k] = 0;
+            if (i < total) {
+                x[k] = i < nu ? (int32_t)(u0 + i) : (int32_t)(a.nU + v0 + (i - nu));
+                c[k] = cnt_load(a, x[k]);
             }
-            scanned++;
         }
-        push_add(a, pb, pc, viol, x, nch, ls);
+#pragma unroll
+        for (int k = 0; k < SCAN_ILP; ++k) {
+            bool viol = false;
+            int nch = 0;
+            if (x[k] >= 0) {
+                const int thr = x[k] < a.nU ? a.thrU : a.thrV;
+                viol = c[k] < thr;
+                if (viol) {
+                    const int pl = __ldcg(&a.plen[x[k]]);
+                    if (a.round0 && pl < thr) viol = false;  // an initial violator: round0 walked it
+                    else nch = pl > 0 ? 1 : 0;               // chunk 0 (see process_items)
+                }
+                scanned++;
+            }
+            push_add(a, pb, pc, viol, x[k] < 0 ? 0 : x[k], nch, ls);
+        }
     }
     push_flush(a, pb, pc);
 }

@@ -83,6 +83,7 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
         knobs.push_back({"hub_degree", {0, 64, 256, 1024}});
         knobs.push_back({"probe_bytes", {12, 16, 24, 32, 64}});
         knobs.push_back({"emit_scatter_max_pct", {0, 5, 25}});
+        knobs.push_back({"emit_bitmap_min_pct", {0, 50, 101}});
         knobs.push_back({"round0", {0, 1}});
     }
     Timer T;

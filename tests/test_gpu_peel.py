@@ -407,3 +407,30 @@ def test_round0_violator_list_longer_than_the_grid():
             mu, mv = core.compute(a, b)
             assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (a, b, r0)
     core.close()
+
+
+@pytest.mark.parametrize("bitmap_pct", [0, 101])
+def test_mask_gather_with_and_without_the_removal_bitmap(bitmap_pct):
+    # the caller-order gather tests removal by bitmap (0: always) or by count (101: never), with
+    # 4-byte mask stores (|U| a multiple of 4, masks aligned; |U| + |V| odd, so the last group
+    # of four ids is partial) or byte stores (an odd |U|, or masks at odd offsets)
+    for nU, nV, seed in [(4000, 2999, 13), (4001, 2999, 14)]:
+        eu, ev = synth.chung_lu_edges(nU, nV, 40000, 2.2, 2.3, seed=seed)
+        off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+        core = ABCore(0)
+        core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+        core.set_param("emit_scatter_max_pct", 0)
+        core.set_param("emit_bitmap_min_pct", bitmap_pct)
+        for mode in (0, 3):
+            core.set_param("mode", mode)
+            for r0 in (0, 1):
+                core.set_param("round0", r0)
+                for a, b in [(1, 1), (2, 3), (4, 4), (7, 2), (12, 12), (0, 5)]:
+                    wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+                    mu, mv = core.compute(a, b)
+                    assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (nU, mode, r0, a, b)
+                    bu = torch.zeros(nU + 1, dtype=torch.uint8, device="cuda")
+                    bv = torch.zeros(nV + 3, dtype=torch.uint8, device="cuda")
+                    core.compute(a, b, bu[1:], bv[3:])
+                    assert np.array_equal(bu[1:].cpu().numpy(), wu) and np.array_equal(bv[3:].cpu().numpy(), wv), ("unaligned", nU, a, b)
+        core.close()
