@@ -7,15 +7,20 @@
 //
 // Up to four launches:
 //  1. k_init: for each candidate x, its count of live candidate neighbours. Per layer, either
-//     (search) a binary search in x's sorted row for the candidate boundary of the other layer,
-//     which equals the count left after removing all initial violators; or (stream) the full
-//     degree, corrected by step 2. Candidates already below their bound are queued.
-//  2. k_stream (only for layers counted by full degree): the rows of the initial violators of
-//     the other layer form one contiguous slice of adj; it is streamed with 16-byte loads and
-//     every entry that hits a candidate decrements it (the paper's first peel round), then
-//     k_scan queues the candidates whose count the stream took below their bound.
+//     (search) the position of the other layer's candidate boundary in x's sorted row -- the
+//     count left after removing all initial violators -- found from where the layer's share of
+//     candidate entries predicts it (peel_core.cuh: row_prefix); or (stream) the full degree,
+//     corrected by step 2. Candidates already below their bound are queued (or, with round0,
+//     listed for step 2).
+//  2. the first peel round, when some count needs it: k_stream (layers counted by full degree:
+//     the rows of the other layer's initial violators form one contiguous slice of adj, streamed
+//     with 16-byte loads) and/or k_round0 (round0: the listed violators' rows); every entry that
+//     hits a candidate decrements it with an atomic that returns nothing. Then k_scan queues the
+//     candidates those decrements took below their bound.
 //  3. k_cascade: the work-queue cascade (peel_core.cuh), then each warp writes its share of
-//     the masks in the caller's ids (gathering each caller id's count through old2new).
+//     the masks in the caller's ids (old2new plus a bitmap of the removed candidates, or a
+//     scatter of the survivors when the candidates are few).
+// The launches after k_init are programmatic dependents of the one before them.
 //
 // With core numbers prepared (coredecomp.cu), the same launches run pruned (Algorithm 2) on the
 // core-ordered copy of the graph: a prefix of each layer is certain to be in the core and is
