@@ -89,7 +89,7 @@ __device__ __forceinline__ void cnt_dec_noret(const PeelArgs &a, int32_t x) {
 }
 
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in
-// cp[x].y (the full degree when its layer's counts came from the full rows).
+// plen[x] (the full degree when its layer's counts came from the full rows).
 __device__ __forceinline__ int row_len_of(const PeelArgs &a, int32_t y) { return __ldcg(&a.plen[y]); }
 
 // Pushes are buffered per warp and queued in bulk: one atomicAdd on the queue's tail reserves
