@@ -261,7 +261,10 @@ int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
  * Among them: "timing" (1: CUDA events around the launches, summed into abcore_stats.kernel_ms),
  * "timing_kinds" (single peel: bit ABCORE_K_* set for each kernel kind timed; default 0xff --
  * an event between two kernels costs the step about as much as a launch), "pdl" (1, default:
- * the single peel's kernels after the count init launch as programmatic dependents). */
+ * the single peel's kernels after the count init launch as programmatic dependents),
+ * "emit_bitmap_min_pct" (0, default: the caller-order mask gather tests removal in a bitmap
+ * that each removal sets; a query with fewer candidates than this percentage of the vertices
+ * reads each candidate's count instead). Results never depend on these parameters. */
 int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
 
 /* Throughput of random 32-bit atomicSub on this device, per second, with the old value returned
