@@ -186,7 +186,10 @@ int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, cons
 int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *betas,
                     uint32_t what, double *best_ms);
 
-/* Wait for work enqueued with ABCORE_ASYNC and return its status. */
+/* Wait for work enqueued with ABCORE_ASYNC and return its status: the first error of any of
+ * those calls. After an error, the masks of every call enqueued since the previous successful
+ * abcore_sync are undefined (a failed peel can leave work state behind for the peels queued after
+ * it); the context itself stays usable, and later calls start from clean state. */
 int abcore_sync(abcore_ctx *ctx);
 
 /* ---- on-the-fly query (Section 5, GFQ) --------------------------------------------------- */
