@@ -86,6 +86,8 @@ typedef struct {
     int32_t grid_blocks;     /* blocks of the persistent cascade launch                        */
     int64_t device_bytes;    /* device memory held by the context now                          */
     int64_t peak_device_bytes;
+    int64_t round0_rows;     /* candidates already below their bound when counted, whose rows
+                                the first round walked without returns ("round0")              */
 } abcore_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------------- */
@@ -149,6 +151,15 @@ int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32
  * beta = 0.6 * alpha_offset. alpha must be at least 1 (with alpha = 0 the upper layer alone is
  * a core for every beta). Errors: EINVAL, ENOTLOADED, ETIMEDOUT. */
 int abcore_alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_offset);
+
+/* The paper's default query (Section 6): delta is the largest core number (Definition 2),
+ * alpha = floor(0.4 * delta) (at least 1), alpha_offset is abcore_alpha_offset(alpha), and
+ * beta = floor(0.6 * alpha_offset). The products are taken in integers (2 * delta / 5 and
+ * 3 * alpha_offset / 5), so the results are exact. Runs the core decomposition on first use, as
+ * abcore_core_numbers does. An empty graph gives delta = 0, alpha = 1, alpha_offset = beta = 0.
+ * Errors: EINVAL (a NULL output), ENOTLOADED, ENOMEM, ETIMEDOUT. */
+int abcore_default_query(abcore_ctx *ctx, int32_t *delta, int32_t *alpha, int32_t *alpha_offset,
+                         int32_t *beta);
 
 /* Community search (Section 5, the Remark after GFQ): the connected component of the
  * (alpha, beta)-core that contains vertex `id` of layer `layer` (0 = U, 1 = V). mask_u[nU] and
@@ -298,26 +309,31 @@ int abcore_export_csr(abcore_ctx *ctx, int64_t *off, int32_t *adj, int32_t *new2
 #define ABCORE_STATIC_MAX_ITEMS    ((1 << 20) + (1 << 16))
 
 /* The (alpha, beta)-core without allocating anything: no cudaMalloc, cudaFree or allocating
- * library routine is called, and no context is needed. It is meant for callers that cannot
- * allocate device memory at run time -- code running inside another framework that owns the
- * device's memory pool, plugins that must not grow a host process's device footprint, or
- * programs that reserve all device memory up front.
+ * library routine is called, and no abcore_ctx is needed (the call runs on the current device).
+ * It is meant for callers that cannot allocate device memory at run time -- code running inside
+ * another framework that owns the device's memory pool, plugins that must not grow a host
+ * process's device footprint, or programs that reserve all device memory up front.
  *   off[nU+nV+1], adj[off[nU+nV]]: the graph in unified ids, on the current device and owned by
  *     the caller: rows 0..nU-1 are the upper vertices and list lower vertices as nU + v, rows
  *     nU..nU+nV-1 are the lower vertices and list upper vertices u; every edge appears in both
- *     rows; rows may be in any order.
+ *     rows; rows may be in any order. adj must hold off[nU+nV] entries.
  *   mask_u[nU], mask_v[nV]: device buffers receiving 1 for core members, else 0.
- *   cuda_stream: the cudaStream_t to run on (NULL = the legacy default stream); the call waits
- *     for its work on that stream before returning.
+ *   cuda_stream: the cudaStream_t to run on (NULL = the legacy default stream). The call reads two
+ *     small values back from the device (the graph's size check, then the status) and waits for
+ *     its stream each time, so its results are ready when it returns.
  * Working memory is one file-scope device array of about 13 MiB, held by every GPU that loads
- * this library until the process exits. Graphs above ABCORE_STATIC_MAX_VERTICES vertices, or
- * whose rows split into more than ABCORE_STATIC_MAX_ITEMS - nU - nV chunks of 1024 entries
- * (about 32 million edges at the vertex limit), are rejected with ABCORE_EINVAL. The first call
- * on each device looks up the array's device address; make that first call before any stream
- * capture. Every call shares the array and it keeps the last call's contents (each call clears
- * what must start empty), so calls that overlap on the GPU -- from several host threads or
- * streams at once -- race and must not be made.
- * Returns ABCORE_OK, ABCORE_EINVAL, ABCORE_ECUDA or ABCORE_ETIMEDOUT. */
+ * this library until the process exits. Rejected with ABCORE_EINVAL: graphs above
+ * ABCORE_STATIC_MAX_VERTICES vertices; graphs whose rows need more than ABCORE_STATIC_MAX_ITEMS
+ * queue items, a row of length d needing ceil(d / 1024) of them (the test is exact: the sum of
+ * ceil(d / 1024) over all nU + nV rows, so at the vertex limit rows of up to 1024 entries always
+ * fit); a negative off[0] or decreasing offsets; an adjacency id outside [0, nU + nV) (found while
+ * peeling: the masks are then undefined). The first call on each device looks up the array's
+ * device address; make that first call before any stream capture. Every call shares the array
+ * and it keeps the last call's contents (each call clears what must start empty), so calls that
+ * overlap on the GPU -- from several host threads or streams at once -- race and must not be made.
+ * Returns ABCORE_OK, ABCORE_EINVAL, ABCORE_ECUDA, ABCORE_ETIMEDOUT (a bounded device wait expired),
+ * or ABCORE_ENOMEM if the removal queue overflowed -- which the size check rules out, so it would
+ * mean an internal fault. */
 int abcore_compute_static(int32_t nU, int32_t nV, const int64_t *off, const int32_t *adj,
                           int32_t alpha, int32_t beta, uint8_t *mask_u, uint8_t *mask_v,
                           void *cuda_stream);

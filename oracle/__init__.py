@@ -15,6 +15,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
 * ``replay``        -- pinned: brute force on tiny update streams.
 * ``components``    -- pinned: scipy.sparse.csgraph.connected_components on random graphs,
   closed forms (no edges, complete bipartite, perfect matchings, paths).
+* ``default_query`` -- pinned: closed form on complete bipartite graphs (delta = min(a, b) and
+  alpha_offset = |U|), and brute force of alpha_offset over every beta on random graphs.
 """
 
 import ctypes
@@ -153,3 +155,73 @@ def components(nU, nV, off, adj):
     if rc != 0:
         raise OracleError(rc, "components")
     return label[: nU + nV], int(nc.value)
+
+
+def default_query(nU, nV, off, adj):
+    """The paper's default query (Section 6), from its definition: delta is the largest core
+    number; alpha = floor(0.4 delta), at least 1; alpha_offset is the largest beta >= 1 whose
+    (alpha, beta)-core is non-empty (0 if none), found by trying beta = 1, 2, ... in turn until the
+    core empties (the nested property makes every larger beta empty too); beta =
+    floor(0.6 alpha_offset). The products are taken in integers. Returns
+    (delta, alpha, alpha_offset, beta)."""
+    core = core_numbers(nU, nV, off, adj)
+    delta = int(core.max()) if core.size else 0
+    alpha = max(1, (2 * delta) // 5)
+    off_beta = 0
+    if nU + nV > 0:
+        beta = 1
+        while True:
+            mu, mv = peel(nU, nV, off, adj, alpha, beta)
+            if int(mu.sum()) + int(mv.sum()) == 0:
+                break
+            off_beta = beta
+            beta += 1
+    return delta, alpha, off_beta, (3 * off_beta) // 5
+
+
+# ------------------------------------------------------------------------------------------
+# Many independent oracle runs side by side. Each run is the plain single-threaded oracle above;
+# host threads only run several of them at once (ctypes releases the GIL during a call), so the
+# checks of a large workload finish in minutes. Nothing is shared between runs but the inputs.
+# ------------------------------------------------------------------------------------------
+def default_threads():
+    return max(1, min(8, (os.cpu_count() or 2) // 2))
+
+
+def peel_many(nU, nV, off, adj, pairs, threads=None):
+    """{(alpha, beta): (mask_u, mask_v, seconds)} for every distinct pair."""
+    import concurrent.futures as cf
+    import time
+
+    def one(p):
+        t = time.perf_counter()
+        mu, mv = peel(nU, nV, off, adj, p[0], p[1])
+        return p, (mu, mv, time.perf_counter() - t)
+
+    with cf.ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
+        return dict(ex.map(one, list(dict.fromkeys(tuple(p) for p in pairs))))
+
+
+def replay_at(nU, nV, eu, ev, op, qu, qv, alpha, beta, ks, threads=None):
+    """{k: (answer, bits, status)} of replay() at the update positions ks. The positions are split
+    into groups of consecutive ones; each group is one replay of the stream up to its last
+    position, checking only the group's positions."""
+    import concurrent.futures as cf
+    ks = sorted(set(int(k) for k in ks))
+    if not ks:
+        return {}
+    t = max(1, min(threads or default_threads(), len(ks)))
+    groups = [ks[i::t] for i in range(t)]
+
+    def one(g):
+        hi = g[-1] + 1
+        check = np.zeros(hi, dtype=np.uint8)
+        check[g] = 1
+        ans, bits, st = replay(nU, nV, eu, ev, op[:hi], qu[:hi], qv[:hi], alpha[:hi], beta[:hi], check)
+        return {k: (int(ans[k]), int(bits[k]), int(st[k])) for k in g}
+
+    out = {}
+    with cf.ThreadPoolExecutor(max_workers=t) as ex:
+        for d in ex.map(one, groups):
+            out.update(d)
+    return out

@@ -173,12 +173,11 @@ class ABCore:
         return int(b.value)
 
     def default_query(self):
-        """The paper's default query: delta = largest core number, alpha = floor(0.4 delta),
-        beta = floor(0.6 alpha_offset(alpha)). Returns (delta, alpha, alpha_offset, beta)."""
-        _, _, delta = self.core_numbers()
-        alpha = max(1, int(0.4 * delta))
-        off = self.alpha_offset(alpha)
-        return delta, alpha, off, int(0.6 * off)
+        """The paper's default query (Section 6), computed by the library: returns
+        (delta, alpha, alpha_offset, beta)."""
+        out = [ctypes.c_int32(0) for _ in range(4)]
+        self._check(abi.abcore_default_query(self._h, *[ctypes.byref(x) for x in out]))
+        return tuple(int(x.value) for x in out)
 
     def community(self, layer, vid, alpha, beta, out_u=None, out_v=None):
         """Masks of the (alpha, beta)-core's component containing vertex vid of layer (0 U, 1 V)."""

@@ -32,7 +32,7 @@ ABCORE_DELETE = 1
 EXPORTED = [
     "abcore_create", "abcore_destroy", "abcore_last_error", "abcore_load_edges", "abcore_load_csr",
     "abcore_compute", "abcore_compute_batch", "abcore_sync", "abcore_components", "abcore_core_numbers", "abcore_autotune",
-    "abcore_alpha_offset", "abcore_community", "abcore_measure_atomics", "abcore_query_edge",
+    "abcore_alpha_offset", "abcore_default_query", "abcore_community", "abcore_measure_atomics", "abcore_query_edge",
     "abcore_serve_start", "abcore_serve_submit", "abcore_serve_poll", "abcore_serve_stop",
     "abcore_get_stats", "abcore_set_param", "abcore_get_param", "abcore_graph_info", "abcore_export_csr",
     "abcore_compute_static",
@@ -56,6 +56,7 @@ class abcore_stats(ctypes.Structure):
         ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64 * K_KINDS),
         ("kernel_ms", ctypes.c_double * K_KINDS), ("mode", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
+        ("round0_rows", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -102,6 +103,7 @@ def load_library(path: str = LIB):
         "abcore_autotune": ([_vp, ctypes.c_int32, _vp, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
                             ctypes.c_int),
         "abcore_alpha_offset": ([_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "abcore_default_query": ([_vp] + [ctypes.POINTER(ctypes.c_int32)] * 4, ctypes.c_int),
         "abcore_community": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                               ctypes.POINTER(ctypes.c_int64), ctypes.c_uint32], ctypes.c_int),
         "abcore_measure_atomics": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
@@ -149,6 +151,7 @@ abcore_components = _fn("abcore_components")
 abcore_core_numbers = _fn("abcore_core_numbers")
 abcore_autotune = _fn("abcore_autotune")
 abcore_alpha_offset = _fn("abcore_alpha_offset")
+abcore_default_query = _fn("abcore_default_query")
 abcore_community = _fn("abcore_community")
 abcore_measure_atomics = _fn("abcore_measure_atomics")
 abcore_query_edge = _fn("abcore_query_edge")

@@ -2,6 +2,7 @@
 // This file validates arguments, moves caller buffers between host and device, and hands the
 // work to the builder (build.cu), the peel (peel.cu), the batch scheduler (batch.cu) and the
 // serving loop (serve.cu).
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -293,6 +294,32 @@ int abcore_alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_offset) {
         return ABCORE_OK;
     }
     return alpha_offset(ctx, alpha, beta_offset);
+}
+
+int abcore_default_query(abcore_ctx *ctx, int32_t *delta, int32_t *alpha, int32_t *alpha_off, int32_t *beta) {
+    if (!ctx) return ABCORE_EINVAL;
+    ctx->err.clear();
+    ABC_CU(cudaSetDevice(ctx->device));
+    ABC_TRY(require_graph(ctx));
+    if (!delta || !alpha || !alpha_off || !beta) return ctx->fail(ABCORE_EINVAL, "NULL output");
+    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(peel_finish(ctx));
+    int32_t d = 0;
+    if (ctx->g.n() > 0) {
+        ABC_TRY(prepare_pruning(ctx));
+        d = ctx->pr.maxcore;
+    }
+    // Section 6: alpha = 0.4 delta and beta = 0.6 alpha_offset, both rounded down (in integers,
+    // so no rounding of 0.4 or 0.6 enters); alpha stays at least 1, the smallest alpha for which
+    // an offset is defined
+    const int32_t a = std::max<int32_t>(1, (int32_t)((2ll * d) / 5));
+    int32_t off = 0;
+    if (ctx->g.n() > 0) ABC_TRY(alpha_offset(ctx, a, &off));
+    *delta = d;
+    *alpha = a;
+    *alpha_off = off;
+    *beta = (int32_t)((3ll * off) / 5);
+    return ABCORE_OK;
 }
 
 int abcore_community(abcore_ctx *ctx, int32_t layer, int32_t id, int32_t alpha, int32_t beta, uint8_t *mask_u,

@@ -1,8 +1,8 @@
 // An (alpha, beta)-core entry point that allocates nothing, for callers that cannot call
 // cudaMalloc: code running where the allocator belongs to someone else (a host framework with a
-// locked memory pool, a plugin inside another application's process, a capture region in which
-// allocation is not allowed) or where device memory is fully reserved ahead of time. The paper
-// has no counterpart; this is an interface convenience around the same peel.
+// locked memory pool, a plugin inside another application's process) or where device memory is
+// fully reserved ahead of time. The paper has no counterpart; this is an interface convenience
+// around the same peel.
 //
 // The caller passes its graph and output masks as device pointers. The working memory -- one
 // count per vertex, the removal queue and a control block -- is a file-scope __device__ array of
@@ -13,6 +13,8 @@
 // device address with cudaGetSymbolAddress, once per device, on the first call made while that
 // device is current. Every call shares the array and finds the previous call's contents in it,
 // so each call clears the parts that must start empty, and calls that overlap on the GPU race.
+// Each call reads two small values back to the host (the graph's queue need, then the error
+// word), so it waits for its stream twice before returning.
 //
 // The peel itself is the plain one: counts start at the full degree, vertices below their
 // bound are queued, and a ticket-queue cascade removes the rest, one exact crossing per vertex.
@@ -40,6 +42,10 @@ struct NaCtl {
     unsigned long long pad2[15];
     int err;
     int pad3[31];
+    unsigned long long chunks;  // queue items the graph needs: sum over rows of ceil(len / chunk)
+    unsigned long long bad;     // rows with a negative length (offsets that decrease)
+    long long m2;               // off[n]: adjacency entries
+    unsigned long long pad4[13];
 };
 
 struct NaScratch {
@@ -83,6 +89,28 @@ __device__ __forceinline__ void na_push(const NaArgs &a, bool want, int32_t x) {
     }
     for (int i = 0; i < nch; ++i)
         abc::st_relaxed(&a.s->q[base + incl - nch + i], ((unsigned long long)(uint32_t)x << 32) | (unsigned)i);
+}
+
+// Checks before anything is queued: the queue items every vertex would need if it fell
+// (ceil(row length / chunk) each; a vertex is queued at most once), off[n], and the offset faults
+// that would send the cascade outside adj -- a negative off[0] or offsets that decrease.
+// (Adjacency ids are checked where the cascade reads them.)
+__global__ void __launch_bounds__(NA_THREADS) k_na_size(const int64_t *off, int64_t n, NaCtl *c) {
+    unsigned long long ch = 0, bad = 0;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = t0; x < n; x += nt) {
+        const int64_t d = off[x + 1] - off[x];
+        if (d < 0) bad++;
+        else ch += (unsigned long long)((d + NA_CHUNK - 1) / NA_CHUNK);
+    }
+    if (t0 == 0 && off[0] < 0) bad++;
+    ch = (unsigned long long)abc::warp_sum64((long long)ch);
+    bad = (unsigned long long)abc::warp_sum64((long long)bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (ch) atomicAdd(&c->chunks, ch);
+        if (bad) atomicAdd(&c->bad, bad);
+    }
+    if (t0 == 0) c->m2 = off[n];
 }
 
 // Counts start at the full degree; vertices below their bound are queued.
@@ -133,8 +161,12 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_cascade(NaArgs a) {
                 int32_t y = 0;
                 if (p < e) {
                     y = a.adj[p];
-                    const int old = atomicSub(&a.s->cnt[y], 1);
-                    push = old == na_thr(a, y);  // the one decrement that crosses below the bound
+                    if (y < 0 || y >= a.nU + a.nV) {  // not a vertex: report it, touch nothing
+                        abc::set_error(&a.s->ctl.err, ABCORE_EINVAL);
+                    } else {
+                        const int old = atomicSub(&a.s->cnt[y], 1);
+                        push = old == na_thr(a, y);  // the one decrement that crosses below the bound
+                    }
                 }
                 na_push(a, push, y);
             }
@@ -198,20 +230,22 @@ extern "C" int abcore_compute_static(int32_t nU, int32_t nV, const int64_t *off,
     }
     NaScratch *s = (NaScratch *)g_na_addr[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int64_t m2 = 0;
-    if (cudaMemcpyAsync(&m2, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return ABCORE_ECUDA;
-    // every vertex is queued at most once as ceil(row / chunk) items
-    if (m2 < 0 || n + m2 / NA_CHUNK + n / NA_CHUNK + 1 > MAXQ) return ABCORE_EINVAL;
-    if (m2 > 0 && !adj) return ABCORE_EINVAL;
-    // the array keeps the previous call's contents: clear the control block and the queue
-    if (cudaMemsetAsync(&s->ctl, 0, sizeof(NaCtl), st) != cudaSuccess ||
-        cudaMemsetAsync(s->q, 0xff, sizeof(unsigned long long) * MAXQ, st) != cudaSuccess)
-        return ABCORE_ECUDA;
-    NaArgs a{off, adj, nU, nV, alpha, beta, mask_u, mask_v, s, 4000ull * 1000000ull};
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the array keeps the previous call's contents: clear the control block, then measure the
+    // graph's queue need (every vertex is queued at most once, as ceil(row / chunk) items)
+    NaCtl size{};
+    if (cudaMemsetAsync(&s->ctl, 0, sizeof(NaCtl), st) != cudaSuccess) return ABCORE_ECUDA;
+    k_na_size<<<(unsigned)std::min<int64_t>((n + NA_THREADS - 1) / NA_THREADS, (int64_t)std::max(sms, 1) * 8),
+                NA_THREADS, 0, st>>>(off, n, &s->ctl);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&size, &s->ctl, sizeof(NaCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ABCORE_ECUDA;
+    if (size.bad != 0 || size.m2 < 0 || size.chunks > (unsigned long long)MAXQ) return ABCORE_EINVAL;
+    if (size.m2 > 0 && !adj) return ABCORE_EINVAL;
+    if (cudaMemsetAsync(s->q, 0xff, sizeof(unsigned long long) * MAXQ, st) != cudaSuccess) return ABCORE_ECUDA;
+    NaArgs a{off, adj, nU, nV, alpha, beta, mask_u, mask_v, s, 4000ull * 1000000ull};
     const unsigned gi = (unsigned)std::min<int64_t>((n + NA_THREADS - 1) / NA_THREADS, (int64_t)sms * 8);
     k_na_init<<<gi, NA_THREADS, 0, st>>>(a);
     k_na_cascade<<<(unsigned)sms * 4, NA_THREADS, 0, st>>>(a);

@@ -626,6 +626,7 @@ int peel_finish(abcore_ctx *ctx) {
         s.scanned += (int64_t)c.st[ST_SCAN];
         s.pushes += (int64_t)c.st[ST_PUSHES];
         s.items += (int64_t)c.st[ST_ITEMS];
+        s.round0_rows += (int64_t)c.l0n;
         if (si.emit == 1) s.emit_gathered += si.n;
         if (si.emit == 2) {
             s.emit_scattered += si.cands;

@@ -68,12 +68,16 @@ struct TargetDev {
     int32_t *mark;     // [n] epoch tags for region / cascade membership
     int32_t *q;        // [2n] scratch queue (a region, then the region vertices it peels)
     int32_t *epoch;    // persisted epoch counter
-    int32_t *rho;      // [n] removal certificate level of non-core vertices (RHO_CORE in C)
-    int32_t *base;     // next unused certificate level
+    int64_t *rho;      // [n] removal certificate level of non-core vertices (RHO_CORE in C)
+    int64_t *base;     // next unused certificate level (64-bit: every re-peel raises it by its
+                       // level count plus one, so a long session would run a 32-bit level out)
     unsigned long long *st;  // [4] regions grown, region vertices, cascades, vertices cascaded
 };
 
-constexpr int32_t RHO_CORE = 0x7fffffff;
+constexpr int64_t RHO_CORE = 0x7fffffffffffffffll;
+// Certificate levels never reach this: a re-peel that would pass it stops the session with
+// ABCORE_ENOMEM instead of wrapping (2^62 levels are far beyond any session's reach).
+constexpr int64_t RHO_LIMIT = 1ll << 62;
 
 struct ServeArgs {
     const int64_t *off;
@@ -241,7 +245,7 @@ __device__ __forceinline__ void bq_push(BlockQueue &Q, int32_t z) { Q.q[atomicAd
 // leaving at cascade level L get certificate level base + L.
 __device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y) {
     __shared__ int tail;
-    __shared__ int32_t base_s;
+    __shared__ int64_t base_s;
     BlockQueue Q{S.q, &tail};
     if (threadIdx.x == 0) {
         tail = 0;
@@ -275,6 +279,7 @@ __device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int3
     }
     if (threadIdx.x == 0 && tail > 0) {
         *S.base = base_s + level + 1;
+        if (*S.base > RHO_LIMIT) abc::set_error(A.err, ABCORE_ENOMEM);
         S.st[2] += 1;
         S.st[3] += (unsigned long long)tail;
     }
@@ -284,7 +289,7 @@ __device__ void delete_cascade(const ServeArgs &A, TargetDev &S, int32_t x, int3
 // Region growth and peel after an insert with an endpoint outside the core (see the header).
 __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32_t y, int32_t ep) {
     __shared__ int tail;
-    __shared__ int32_t base_s;
+    __shared__ int64_t base_s;
     BlockQueue Q{S.q, &tail};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -309,7 +314,7 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
         __syncthreads();
         for (int i = head + warp; i < end; i += SERVE_WARPS) {
             const int32_t w = S.q[i];
-            const int32_t rw = S.rho[w];
+            const int64_t rw = S.rho[w];
             for_neighbours(A, S, w, [&](int32_t z) {
                 if (!S.M[z] && S.rho[z] > rw && S.deg[z] >= thr_of(A, S, z)) {
                     const int old = atomicExch(&S.mark[z], ep);
@@ -382,6 +387,7 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
     }
     if (threadIdx.x == 0) {
         *S.base = base_s + level + 1;
+        if (*S.base > RHO_LIMIT) abc::set_error(A.err, ABCORE_ENOMEM);
         S.st[0] += 1;
         S.st[1] += (unsigned long long)R;
     }
@@ -892,8 +898,8 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
                 h[0] = h[1];
                 ++round;
             }
-            const int32_t base0 = round + 2;
-            ABC_CU(cudaMemcpyAsync(T.base, &base0, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+            const int64_t base0 = (int64_t)round + 2;
+            ABC_CU(cudaMemcpyAsync(T.base, &base0, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
             ABC_CU(cudaStreamSynchronize(ctx->stream));
         }
         ABC_CU(cudaGetLastError());

@@ -8,14 +8,14 @@ sharing any of the method's code.
 
 from .rng import mix32, uniform53, derive_key
 from .chung_lu import layer_weights, chung_lu_edges
-from .stream import edge_update_stream, StreamOp
-from .grids import log_grid, grid_pairs
+from .stream import edge_update_stream, StreamOp, sample_positions
+from .grids import log_grid, grid_pairs, sampled_pairs
 from .workloads import WORKLOADS, make_graph
 
 __all__ = [
     "mix32", "uniform53", "derive_key",
     "layer_weights", "chung_lu_edges",
-    "edge_update_stream", "StreamOp",
-    "log_grid", "grid_pairs",
+    "edge_update_stream", "StreamOp", "sample_positions",
+    "log_grid", "grid_pairs", "sampled_pairs",
     "WORKLOADS", "make_graph",
 ]

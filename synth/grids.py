@@ -26,3 +26,20 @@ def log_grid(k: int, lo: int, hi: int):
 def grid_pairs(k: int, lo: int, hi: int):
     g = log_grid(k, lo, hi)
     return [(a, b) for a in g for b in g]
+
+
+def sampled_pairs(grid, limit):
+    """Pairs of a grid to check against a slow reference: the four corners first, then the first
+    and last beta of each alpha's chain, then the diagonal, up to `limit` distinct pairs."""
+    al = sorted({p[0] for p in grid})
+    be = sorted({p[1] for p in grid})
+    order = [(al[0], be[0]), (al[0], be[-1]), (al[-1], be[0]), (al[-1], be[-1])]
+    for a in al[1:-1]:
+        order += [(a, be[-1]), (a, be[0])]
+    order += [(a, b) for a, b in zip(al, be)]
+    gs = set(map(tuple, grid))
+    out = []
+    for p in order:
+        if p in gs and p not in out:
+            out.append(p)
+    return out[:limit]

@@ -112,3 +112,16 @@ def edge_update_stream(eu: np.ndarray, ev: np.ndarray, nU: int, nV: int, n_ops: 
     target = np.minimum((r_tg * n_targets).astype(np.int64), n_targets - 1).astype(np.int8)
     t_unit = np.cumsum(-np.log1p(-r_arr))
     return StreamOp(op=op, u=uu, v=vv, target=target, t_unit=t_unit)
+
+
+def sample_positions(stream: StreamOp, n_targets: int, per: int):
+    """Update positions to check against a slow reference: for each kind of update and each
+    target, `per` positions spread evenly over the stream, plus the first and the last update."""
+    n = len(stream)
+    ks = {0, n - 1} if n else set()
+    for opk in (0, 1):
+        for t in range(n_targets):
+            idx = np.nonzero((stream.op == opk) & (stream.target == t))[0]
+            if len(idx):
+                ks.update(int(idx[j]) for j in np.linspace(0, len(idx) - 1, min(per, len(idx))).astype(np.int64))
+    return sorted(ks)

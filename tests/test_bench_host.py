@@ -46,14 +46,34 @@ def test_traffic_is_reported_only_for_the_recorded_digest(tree):
 
 
 def test_algorithmic_bytes_per_kernel_kind():
+    # the survey's per-unit figures: 8 B offsets + 4 B count per scanned vertex, 1 B mask per
+    # vertex, 16 B offsets + 8 B queue per removed vertex, 4 B per entry, 8 B per decrement,
+    # 4 B per frontier check; everything else the design moves is overhead, kept apart
     st = dict(init_vertices=10, search_probes=7, stream_entries=100, stream_decrements=40,
               scanned=20, decrements=70, items=5, entries=50, pushes=6, emit_gathered=64,
-              emit_scattered=0)
-    b = bench.algorithmic_bytes(st)
-    assert b[0] == 16 * 10 + 4 * 7
-    assert b[1] == 4 * 100 + 8 * 40 + 4 * 20
-    # cascade: items, entries, its own decrements (70 - 40), push slots, the gather (5.25 B a
-    # vertex) and the removal bits (8 B a push)
-    assert b[2] == 28 * 5 + 4 * 50 + 8 * 30 + 8 * 6 + 5.25 * 64 + 8 * 6
-    st.update(emit_gathered=0, emit_scattered=9)
-    assert bench.algorithmic_bytes(st)[2] == 28 * 5 + 4 * 50 + 8 * 30 + 8 * 6 + 4 * 9
+              emit_scattered=0, mask_zeroed=0, round0_rows=2)
+    alg, over = bench.algorithmic_bytes(st)
+    assert alg[0] == 12 * 10 + 4 * 7 and over[0] == 4 * 10 + 28 * 7
+    assert alg[1] == 4 * 100 + 8 * 40 + 4 * 20 + 24 * 2 and over[1] == 8 * 2
+    # cascade: the 6 - 2 vertices its queue carried, its entries, its own decrements (70 - 40),
+    # and one mask byte per vertex; overhead: queue bytes beyond 24 B a removed vertex, the
+    # gather's id and bitmap reads (4.25 B a vertex) and the removal bits (8 B a removal)
+    assert alg[2] == 24 * 4 + 4 * 50 + 8 * 30 + 64
+    assert over[2] == (36 * 5 - 24 * 4) + 4.25 * 64 + 8 * 4
+    st.update(emit_gathered=0, emit_scattered=9, mask_zeroed=64)
+    alg, over = bench.algorithmic_bytes(st)
+    assert alg[2] == 24 * 4 + 4 * 50 + 8 * 30 + 64
+    assert over[2] == (36 * 5 - 24 * 4) + 4 * 9
+
+
+def test_sampled_grid_pairs_cover_corners_and_chain_ends():
+    import synth
+    grid = synth.grid_pairs(8, 1, 1024)
+    s8 = bench.sampled_grid_pairs(grid, 8)
+    assert s8[:4] == [(1, 1), (1, 1024), (1024, 1), (1024, 1024)] and len(set(s8)) == 8
+    g16 = synth.grid_pairs(16, 1, 512)
+    s = bench.sampled_grid_pairs(g16, 36)
+    # every chain's first and last beta, and nothing outside the grid
+    for a in sorted({p[0] for p in g16}):
+        assert (a, 1) in s and (a, 512) in s
+    assert set(s) <= set(g16) and len(s) == 36 and len(set(s[:32])) == 32

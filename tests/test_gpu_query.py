@@ -47,12 +47,21 @@ def test_alpha_offset_and_default_query(small):
         assert core.alpha_offset(alpha) == _oracle_offset(nU, nV, off, adj, alpha), alpha
     with pytest.raises(ABCoreError):
         core.alpha_offset(0)
-    delta, alpha, offset, beta = core.default_query()
-    cn = oracle.core_numbers(nU, nV, off, adj)
-    assert delta == int(cn.max())
-    assert alpha == max(1, int(0.4 * delta))
-    assert offset == _oracle_offset(nU, nV, off, adj, alpha)
-    assert beta == int(0.6 * offset)
+    # the library computes the whole default query; the oracle restates it from the paper
+    assert core.default_query() == oracle.default_query(nU, nV, off, adj)
+
+
+@pytest.mark.parametrize("a,b", [(5, 7), (7, 5), (3, 3), (12, 2), (1, 9)])
+def test_default_query_complete_bipartite_matches_oracle(a, b):
+    # K_{a,b}: every (alpha, beta)-core with alpha <= b and beta <= a is the whole graph
+    uu, vv = np.meshgrid(np.arange(a), np.arange(b), indexing="ij")
+    eu, ev = uu.ravel().astype(np.int32), vv.ravel().astype(np.int32)
+    off, adj = oracle.build_csr(a, b, eu, ev)
+    core = ABCore(0)
+    core.load_edges(a, b, eu, ev)
+    got = core.default_query()
+    core.close()
+    assert got == oracle.default_query(a, b, off, adj)
 
 
 def _oracle_community(nU, nV, off, adj, eu, ev, q, alpha, beta):

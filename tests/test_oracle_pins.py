@@ -377,3 +377,44 @@ def test_components_closed_forms():
     # path u0 - v0 - u1 - v1 - u2 plus an isolated v2
     lab, nc = _components_edges(3, 3, [(0, 0), (1, 0), (1, 1), (2, 1)])
     assert nc == 2 and list(lab) == [0, 0, 0, 0, 0, 5]
+
+
+# ------------------------------------------------------------------------------------------
+# The paper's default query (Section 6)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("a,b", [(5, 7), (7, 5), (3, 3), (12, 2), (1, 9), (10, 10)])
+def test_default_query_complete_bipartite_closed_form(a, b):
+    # K_{a,b} (|U| = a, |L| = b): the k-core numbers are all min(a, b), and an (alpha, beta)-core
+    # with alpha <= b is the whole graph for beta <= a and empty beyond, so alpha_offset = a
+    edges = [(u, v) for u in range(a) for v in range(b)]
+    eu = np.array([e[0] for e in edges], dtype=np.int32)
+    ev = np.array([e[1] for e in edges], dtype=np.int32)
+    off, adj = oracle.build_csr(a, b, eu, ev)
+    delta, alpha, offset, beta = oracle.default_query(a, b, off, adj)
+    assert delta == min(a, b)
+    assert alpha == max(1, (2 * min(a, b)) // 5)
+    assert offset == a
+    assert beta == (3 * a) // 5
+
+
+def test_default_query_offset_by_brute_force():
+    # alpha_offset checked against subset enumeration (Definition 1 read literally) for every
+    # beta, and delta against networkx's core numbers
+    rng = random.Random(17)
+    for trial in range(12):
+        nU, nV = rng.randint(2, 6), rng.randint(2, 6)
+        edges = _random_graph(rng, nU, nV, 0.6)
+        eu = np.array([e[0] for e in edges], dtype=np.int32)
+        ev = np.array([e[1] for e in edges], dtype=np.int32)
+        off, adj = oracle.build_csr(nU, nV, eu, ev)
+        delta, alpha, offset, beta = oracle.default_query(nU, nV, off, adj)
+        G = nx.Graph()
+        G.add_nodes_from(range(nU + nV))
+        G.add_edges_from((u, nU + v) for u, v in edges)
+        assert delta == max(nx.core_number(G).values())
+        want = 0
+        for bb in range(1, nU + 2):
+            if max_feasible(nU, nV, edges, alpha, bb):
+                want = bb
+        assert offset == want, (trial, edges)
+        assert beta == (3 * want) // 5
