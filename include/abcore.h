@@ -88,6 +88,8 @@ typedef struct {
     int64_t peak_device_bytes;
     int64_t round0_rows;     /* candidates already below their bound when counted, whose rows
                                 the first round walked without returns ("round0")              */
+    int64_t scope_queries;   /* on-the-fly queries answered with the component scope            */
+    int64_t scope_vertices;  /* vertices those queries re-peeled (their components' sizes)      */
 } abcore_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------------- */
@@ -207,9 +209,17 @@ int abcore_sync(abcore_ctx *ctx);
 
 /* Apply the edge update (u, v) -- op ABCORE_INSERT or ABCORE_DELETE -- to the loaded graph
  * (it persists), then set *in_core to 1 iff both u and v belong to the (alpha, beta)-core of
- * the updated graph, else 0. Only the region the update can affect is re-peeled.
+ * the updated graph, else 0. The "query_scope" parameter picks what is re-peeled; both give the
+ * same answers:
+ *   0 (default): only the region the update can affect, from the target core kept by the
+ *      serving loop (a delete cascades inside the core; an insert peels the non-core vertices
+ *      reachable along the removal certificate; see abcore_serve_start);
+ *   1: the paper's scope -- the connected component(s) of u and v in the updated graph, peeled
+ *      from scratch (Algorithm 1 on the component's induced subgraph). The component forest is
+ *      kept current: an insert unites two components, a delete recomputes the components of the
+ *      one it may split. abcore_stats.scope_vertices counts the vertices re-peeled.
  * Errors: EINVAL, ENOTLOADED, EEXIST (insert of a present edge), ENOENT (delete of an
- * absent edge); on those the graph is unchanged. */
+ * absent edge); on those the graph is unchanged and *in_core reports the current core. */
 int abcore_query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta,
                       uint8_t *in_core);
 
@@ -249,10 +259,14 @@ typedef struct {
 /* Start serving with n_targets (alpha, beta) targets and a request ring of ring_slots entries.
  * Updates are applied in submission order and every answer is the one the update would get
  * if requests were processed one at a time, so answers do not depend on timing or batching.
- * Each target keeps its own device view of the updates; inserted edges live in a pool sized by
- * the "serve_inserts" parameter (default 2^20 inserts, 32 bytes each per target): once it is
- * full the loop stops with ABCORE_ENOMEM, reported by the next submit, poll or stop; the
- * session's view of the graph is then unusable and the context must be destroyed. */
+ * Each target keeps its own device view of the updates; inserted edges live in a pool per target,
+ * first sized by the "serve_inserts" parameter (default 2^20 inserts, 32 bytes each). Requests
+ * are admitted by memory: an insert that does not fit its target's pool is held back, with the
+ * view unchanged, until the library has doubled that pool (from the next submit, poll or stop
+ * call), and is then processed in its turn -- answers are the same as with a large pool. Held
+ * requests keep their ring slots, so submits meanwhile may return EBUSY. If the device has no
+ * memory for the larger pool, that call returns ABCORE_ENOMEM and the requests keep waiting (a
+ * later call tries again); the session stays usable. */
 int abcore_serve_start(abcore_ctx *ctx, const int32_t *target_alphas, const int32_t *target_betas,
                        int32_t n_targets, int32_t ring_slots);
 

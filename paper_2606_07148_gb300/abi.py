@@ -56,7 +56,7 @@ class abcore_stats(ctypes.Structure):
         ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64 * K_KINDS),
         ("kernel_ms", ctypes.c_double * K_KINDS), ("mode", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
-        ("round0_rows", ctypes.c_int64),
+        ("round0_rows", ctypes.c_int64), ("scope_queries", ctypes.c_int64), ("scope_vertices", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -3,6 +3,7 @@
 // work to the builder (build.cu), the peel (peel.cu), the batch scheduler (batch.cu) and the
 // serving loop (serve.cu).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -20,6 +21,7 @@ int require_graph(abcore_ctx *ctx) {
 void drop_derived(abcore_ctx *ctx) {
     free_batch(ctx);
     free_serve(ctx);
+    free_gfq(ctx);
     free_peel(ctx);
 }
 
@@ -47,6 +49,7 @@ int abcore_create(abcore_ctx **out, int device, void *cuda_stream) {
     abcore_ctx *ctx = new (std::nothrow) abcore_ctx();
     if (!ctx) return ABCORE_ENOMEM;
     ctx->device = device;
+    if (const char *lv = getenv("ABCORE_LOG")) ctx->prm.log_level = std::max(0, std::min(2, atoi(lv)));
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         delete ctx;
@@ -172,7 +175,7 @@ int abcore_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *mask_u
     if ((g.nU > 0 && !mask_u) || (g.nV > 0 && !mask_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
     const bool dev = ptr_on_device(flags);
     if ((flags & ABCORE_ASYNC) && !dev) return ctx->fail(ABCORE_EINVAL, "ABCORE_ASYNC needs device pointers");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     if (g.n() == 0) return ABCORE_OK;
     if (ctx->prm.algo == 2 && !ctx->pr.ready) {
         ABC_TRY(peel_finish(ctx));
@@ -204,7 +207,7 @@ int abcore_compute_batch(abcore_ctx *ctx, int32_t n, const int32_t *alphas, cons
     if ((g.nU > 0 && !masks_u) || (g.nV > 0 && !masks_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
     const bool dev = ptr_on_device(flags);
     if ((flags & ABCORE_ASYNC) && !dev) return ctx->fail(ABCORE_EINVAL, "ABCORE_ASYNC needs device pointers");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     if (g.n() == 0) return ABCORE_OK;
     ABC_TRY(peel_finish(ctx));
     if (dev) return batch_compute(ctx, n, alphas, betas, masks_u, masks_v, !(flags & ABCORE_ASYNC));
@@ -233,7 +236,7 @@ int abcore_core_numbers(abcore_ctx *ctx, int32_t *core_u, int32_t *core_v, int32
     ABC_TRY(require_graph(ctx));
     const Graph &g = ctx->g;
     if ((g.nU > 0 && !core_u) || (g.nV > 0 && !core_v)) return ctx->fail(ABCORE_EINVAL, "NULL core array");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     ABC_TRY(peel_finish(ctx));
     if (g.n() == 0) {
         if (max_core) *max_core = 0;
@@ -268,7 +271,8 @@ int abcore_components(abcore_ctx *ctx, int32_t *label_u, int32_t *label_v, int64
         du = tmp;
         dv = tmp + g.nU;
     }
-    int rc = ctx->serve ? serve_components(ctx, du, dv, n_components) : components_compute(ctx, du, dv, n_components);
+    int rc = ctx->gfq ? serve_materialize(ctx) : ABCORE_OK;  // queried updates become the CSR first
+    if (!rc) rc = ctx->serve ? serve_components(ctx, du, dv, n_components) : components_compute(ctx, du, dv, n_components);
     if (!rc && tmp) {
         cudaError_t e = cudaSuccess;
         if (g.nU) e = cudaMemcpyAsync(label_u, du, sizeof(int32_t) * g.nU, cudaMemcpyDeviceToHost, ctx->stream);
@@ -288,7 +292,7 @@ int abcore_alpha_offset(abcore_ctx *ctx, int32_t alpha, int32_t *beta_offset) {
     ABC_TRY(require_graph(ctx));
     // with alpha = 0 the upper layer alone is a core for every beta: no offset exists
     if (alpha < 1 || !beta_offset) return ctx->fail(ABCORE_EINVAL, "alpha must be >= 1 and beta_offset non-NULL");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     if (ctx->g.n() == 0) {
         *beta_offset = 0;
         return ABCORE_OK;
@@ -302,7 +306,7 @@ int abcore_default_query(abcore_ctx *ctx, int32_t *delta, int32_t *alpha, int32_
     ABC_CU(cudaSetDevice(ctx->device));
     ABC_TRY(require_graph(ctx));
     if (!delta || !alpha || !alpha_off || !beta) return ctx->fail(ABCORE_EINVAL, "NULL output");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     ABC_TRY(peel_finish(ctx));
     int32_t d = 0;
     if (ctx->g.n() > 0) {
@@ -333,7 +337,7 @@ int abcore_community(abcore_ctx *ctx, int32_t layer, int32_t id, int32_t alpha, 
     if (layer != 0 && layer != 1) return ctx->fail(ABCORE_EINVAL, "layer must be 0 (U) or 1 (V)");
     if (id < 0 || id >= (layer == 0 ? g.nU : g.nV)) return ctx->fail(ABCORE_EINVAL, "vertex id out of range");
     if ((g.nU > 0 && !mask_u) || (g.nV > 0 && !mask_v)) return ctx->fail(ABCORE_EINVAL, "NULL mask");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     ABC_TRY(peel_finish(ctx));
     int32_t q = 0;
     ABC_CU(cudaMemcpyAsync(&q, g.old2new + (layer == 0 ? 0 : g.nU) + id, sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -368,7 +372,7 @@ int abcore_autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int
     if (!(what & ABCORE_TUNE_BATCH) && n > CTL_RING) return ctx->fail(ABCORE_EINVAL, "at most %d queries per sample", CTL_RING);
     for (int32_t i = 0; i < n; ++i)
         if (alphas[i] < 0 || betas[i] < 0) return ctx->fail(ABCORE_EINVAL, "alpha and beta must be >= 0");
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     ABC_TRY(peel_finish(ctx));
     if (ctx->g.n() == 0) {
         if (best_ms) *best_ms = 0;
@@ -526,6 +530,12 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
     } else if (k == "serve_inserts") {
         if (value < 1 || value > (1 << 29)) return ctx->fail(ABCORE_EINVAL, "serve_inserts must be in [1, 2^29]");
         p.serve_inserts = value;
+    } else if (k == "log_level") {
+        if (value < 0 || value > 2) return ctx->fail(ABCORE_EINVAL, "log_level must be 0..2");
+        p.log_level = (int)value;
+    } else if (k == "query_scope") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "query_scope must be 0 (certificate) or 1 (component)");
+        p.query_scope = (int)value;
     } else if (k == "algo") {
         if (value < 0 || value > 2) return ctx->fail(ABCORE_EINVAL, "algo must be 0 (auto), 1 (GCC) or 2 (GCC+)");
         p.algo = (int)value;
@@ -567,6 +577,8 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "timing_kinds") *value = p.timing_kinds;
     else if (k == "serve_inserts") *value = p.serve_inserts;
     else if (k == "algo") *value = p.algo;
+    else if (k == "query_scope") *value = p.query_scope;
+    else if (k == "log_level") *value = p.log_level;
     else return ctx->fail(ABCORE_EINVAL, "unknown parameter '%s'", name);
     return ABCORE_OK;
 }
@@ -589,7 +601,7 @@ int abcore_export_csr(abcore_ctx *ctx, int64_t *off, int32_t *adj, int32_t *new2
     ABC_CU(cudaSetDevice(ctx->device));
     ABC_TRY(require_graph(ctx));
     ABC_TRY(abcore_sync(ctx));
-    if (ctx->serve) ABC_TRY(serve_materialize(ctx));
+    ABC_TRY(serve_materialize(ctx));
     const Graph &g = ctx->g;
     const cudaMemcpyKind kind = ptr_on_device(flags) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (off) ABC_CU(cudaMemcpyAsync(off, g.off, sizeof(int64_t) * (g.n() + 1), kind, ctx->stream));

@@ -70,6 +70,9 @@ struct BatchArgs {
     uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
+    // optional timeline: prof[c * (MAX_STEPS + 2) + j] = globaltimer when chain c's block 0 starts
+    // (j = 0) and when its step j - 1 has closed (j >= 1); nullptr: not recorded
+    unsigned long long *prof;
 };
 
 __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
@@ -121,6 +124,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     LaneStats ls;
     unsigned long long probes = 0, inits = 0, ents = 0, sdecs = 0;
 
+    unsigned long long *prof = B.prof != nullptr && r == 0 && threadIdx.x == 0 ? B.prof + (size_t)c * (MAX_STEPS + 2)
+                                                                               : nullptr;
+    if (prof) prof[0] = abc::now_ns();
     abc::init_range(a, smem[wib].push, t0, nthreads, ls, probes, inits);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     if (cd.ea > cd.sa || cd.eb > cd.sb) {
@@ -137,6 +143,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     // block waits on warps that left, and the barrier reports the error to all of them.
     (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+    if (prof) prof[1] = abc::now_ns();
     for (int j = 1; j < cd.nsteps; ++j) {
         const int32_t prev = a.thrV;
         a.thrV = B.betas[cd.beta_off + j];
@@ -161,6 +168,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
+        if (prof) prof[j + 1] = abc::now_ns();
     }
 out:
     abc::flush_stats(a, ls);
@@ -255,6 +263,7 @@ struct BatchState {
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    unsigned long long *prof = nullptr;  // [waves x MAX_CHAINS_PER_WAVE x (MAX_STEPS + 2)] (log level 2)
 };
 
 static void destroy_plan(abcore_ctx *ctx, BatchState *b) {
@@ -269,6 +278,7 @@ static void destroy_plan(abcore_ctx *ctx, BatchState *b) {
     }
     b->waves.clear();
     ctx->release(b->d_betas);
+    ctx->release(b->prof);
     if (b->ctl_host) cudaFreeHost(b->ctl_host);
     b->ctl_host = nullptr;
     b->key_a.clear();
@@ -390,6 +400,10 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
         }
     }
     ABC_CU(cudaMallocHost(&b->ctl_host, sizeof(PeelCtl) * MAX_CHAINS_PER_WAVE * b->waves.size()));
+    if (ctx->prm.log_level >= 2)
+        ABC_TRY(ctx->alloc(&b->prof, b->waves.size() * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2), "batch timeline"));
+    ctx->log(1, "batch plan: %d pairs, %d chains in %d waves of up to %d, grid %d blocks", n, C, (int)b->waves.size(),
+             per_wave, grid);
     return ABCORE_OK;
 }
 
@@ -475,6 +489,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.flush_steps = ctx->prm.flush_steps;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
+        B.prof = b->prof ? b->prof + wi * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2) : nullptr;
         void *args[] = {&B};
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(w.grid);
@@ -592,6 +607,26 @@ int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32
             s.items += (int64_t)pc.st[ST_ITEMS];
         }
     for (auto &w : b->waves) s.emit_gathered += (int64_t)w.pairs.size() * g.n();
+    if (b->prof && ctx->prm.log_level >= 2) {
+        // per chain: the wave, alpha, and each step's duration in microseconds (step 0 includes
+        // the count init and the first round)
+        std::vector<unsigned long long> h(b->waves.size() * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2));
+        if (cudaMemcpy(h.data(), b->prof, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            for (size_t wi = 0; wi < b->waves.size(); ++wi)
+                for (size_t c = 0; c < b->waves[wi].chains.size(); ++c) {
+                    const ChainDev &cd = b->waves[wi].chains[c];
+                    const unsigned long long *t = h.data() + (wi * MAX_CHAINS_PER_WAVE + c) * (MAX_STEPS + 2);
+                    std::string line;
+                    char tmp[32];
+                    for (int j = 0; j < cd.nsteps; ++j) {
+                        snprintf(tmp, sizeof(tmp), " %.1f", (double)(t[j + 1] - t[j]) / 1e3);
+                        line += tmp;
+                    }
+                    ctx->log(2, "batch wave %zu chain alpha=%d blocks=%d total %.1f us; steps:%s", wi, cd.alpha,
+                             cd.nblocks, (double)(t[cd.nsteps] - t[0]) / 1e3, line.c_str());
+                }
+        }
+    }
     if (timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) {

@@ -145,6 +145,12 @@ int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStr
     const int64_t n = g.n();
     const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16));
     k_cc_init<<<gi, 256, 0, st>>>(parent, n);
+    ctx->stats.launches++;
+    return cc_hook_rows(ctx, parent, tomb, st, keep);
+}
+
+int cc_hook_rows(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st, const uint8_t *keep) {
+    const Graph &g = ctx->g;
     // U rows by length (internal U ids are sorted by non-increasing degree)
     const int32_t h = (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, CC_HUB), g.nU);
     const int32_t w = (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, CC_MEDIUM), g.nU);
@@ -159,7 +165,7 @@ int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStr
         k_cc_hook_thread<<<(unsigned)std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->num_sms * 16), 256, 0, st>>>(
             g.off, g.adj, tomb, keep, parent, w, g.nU);
     }
-    ctx->stats.launches += 4;
+    ctx->stats.launches += 3;
     ABC_CU(cudaGetLastError());
     return ABCORE_OK;
 }

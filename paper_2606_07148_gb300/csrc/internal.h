@@ -129,7 +129,12 @@ struct Params {
     int timing_kinds = 0xff;   // single peel: the kernel kinds (bit ABCORE_K_*) timed. An event
                                // between two kernels costs the step about as much as a launch, so
                                // a measurement may time only the kind it reports.
-    int64_t serve_inserts = 1 << 20;  // inserted edges each served target can hold (ENOMEM beyond)
+    int64_t serve_inserts = 1 << 20;  // inserted edges each served target's pool first holds (it
+                                      // doubles whenever an insert does not fit)
+    int log_level = 0;         // diagnostics on stderr: 0 none, 1 plans and events, 2 also the
+                               // batch's per-step timeline (initial value from ABCORE_LOG)
+    int query_scope = 0;       // abcore_query_edge: 0 the certificate scope (serving loop), 1 the
+                               // paper's scope -- the endpoints' components re-peeled from scratch
     int algo = 0;              // abcore_compute: 0 GCC+ when core numbers are prepared and it has
                                // fewer vertices to peel, else GCC; 1 always GCC; 2 always GCC+
                                // (prepares core numbers on first use)
@@ -199,6 +204,7 @@ struct Pruning {
 
 struct BatchState;
 struct ServeState;
+struct GfqState;
 
 struct abcore_ctx {
     int device = 0;
@@ -216,8 +222,19 @@ struct abcore_ctx {
     int init_blocks = 0;     // resident k_init blocks (occupancy x SMs)
     BatchState *batch = nullptr;
     ServeState *serve = nullptr;
+    GfqState *gfq = nullptr;   // on-the-fly queries with the component scope (query_scope = 1)
     bool pending_async = false;
 
+    // diagnostics at `level` or below the "log_level" parameter, one line on stderr
+    void log(int level, const char *fmt, ...) {
+        if (prm.log_level < level) return;
+        char buf[1024];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        fprintf(stderr, "[abcore] %s\n", buf);
+    }
     int fail(int code, const char *fmt, ...) {
         char buf[512];
         va_list ap;
@@ -330,13 +347,17 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
 int serve_submit(abcore_ctx *ctx, const abcore_req *reqs, int32_t n, uint64_t *seq_out);
 int serve_poll(abcore_ctx *ctx, abcore_resp *out, int32_t max, int32_t *n_out);
 int serve_stop(abcore_ctx *ctx);
-int serve_materialize(abcore_ctx *ctx);  // rebuild the CSR if served updates changed the graph
+int serve_materialize(abcore_ctx *ctx);  // rebuild the CSR if served or queried updates changed the graph
 void free_serve(abcore_ctx *ctx);
+void free_gfq(abcore_ctx *ctx);
 int serve_components(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
 
 // components.cu -- connected components (union-find)
 int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st,
                  const uint8_t *keep = nullptr);
+// the unions of cc_hook_base without resetting the forest first (base rows minus tombstones,
+// edges with both endpoints kept)
+int cc_hook_rows(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st, const uint8_t *keep);
 int community_compute(abcore_ctx *ctx, const uint8_t *d_alive, int32_t q_internal, uint8_t *d_mask_u,
                       uint8_t *d_mask_v, int64_t *size);
 int cc_emit(abcore_ctx *ctx, int32_t *parent, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp, cudaStream_t st);

@@ -95,6 +95,7 @@ struct ServeArgs {
     unsigned long long *progress_dev;   // device: requests processed, per target
     unsigned long long *exit_at;        // device: ~0, or the request count every block stops at
     int *err;                           // device: first error
+    int *grow;                          // device, per target: 1 once its inserted-edge pool is full
     int32_t *comp;                      // component union-find over the current graph
     int *comp_stale;                    // set once a delete may have split a component
     int32_t slots;
@@ -394,9 +395,25 @@ __device__ void insert_region(const ServeArgs &A, TargetDev &S, int32_t x, int32
     __syncthreads();
 }
 
-// One update against one target's view. Returns the status; *bits = (u in C) | (v in C) << 1.
-__device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t x, int32_t y, int32_t ep,
-                              int *bits) {
+// Pool entries an append to a segment needs: a new segment of 2, or twice the room of a full one.
+__device__ __forceinline__ int64_t append_need(int2 seg) {
+    if (seg.x < 0) return 2;
+    const int32_t cap = ins_capacity(seg.y);
+    return seg.y == cap ? 2 * (int64_t)cap : 0;
+}
+
+// Whether an edge (x, y) fits in the target's inserted-edge pool (the two appends together).
+__device__ __forceinline__ int pool_room(const TargetDev &S, int32_t x, int32_t y) {
+    return (int64_t)*S.pool_top + append_need(S.ins[x]) + append_need(S.ins[y]) <= (int64_t)S.pool_cap;
+}
+
+// process_update's answer when the target's pool has no room for an insert (not a status the
+// caller sees: the request is held back and processed again once the pool has grown)
+constexpr int POOL_FULL = 1;
+
+// The edge change of one update on a view: presence test, then tombstone / inserted-segment
+// change and degrees. Returns the status, or POOL_FULL with the view unchanged.
+__device__ int apply_update(const ServeArgs &A, TargetDev &S, int op, int32_t x, int32_t y) {
     __shared__ int status_s;
     const int64_t px = cta_find(A.adj, __ldg(&A.off[x]), __ldg(&A.off[x + 1]), y);
     int64_t py = -1;
@@ -410,6 +427,14 @@ __device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t 
     int st = ABCORE_OK;
     if (op == ABCORE_INSERT && present) st = ABCORE_EEXIST;
     if (op == ABCORE_DELETE && !present) st = ABCORE_ENOENT;
+    if (st == ABCORE_OK && op == ABCORE_INSERT && px < 0) {
+        // admission by memory: the new edge needs room in both endpoints' pool segments. With no
+        // room, nothing changes and the request waits for the host to grow the pool.
+        __shared__ int room_s;
+        if (threadIdx.x == 0) room_s = pool_room(S, x, y);
+        __syncthreads();
+        if (!room_s) return POOL_FULL;
+    }
     if (st == ABCORE_OK) {
         if (op == ABCORE_INSERT) {
             if (px >= 0) {
@@ -418,7 +443,7 @@ __device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t 
                     tomb_set(S.tomb, py, false);
                 }
             } else if (!ins_append(A, S, x, y) || !ins_append(A, S, y, x)) {
-                st = ABCORE_ENOMEM;  // the loop stops: the pool error ends every block
+                st = ABCORE_ENOMEM;  // cannot happen after pool_room; the error ends the loop
             }
             if (threadIdx.x == 0 && st == ABCORE_OK) {
                 S.deg[x]++;
@@ -445,6 +470,17 @@ __device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t 
     }
     if (threadIdx.x == 0) status_s = st;
     __syncthreads();
+    const int r = status_s;
+    __syncthreads();
+    return r;
+}
+
+// One update against one target's view: the edge change (apply_update), then the scoped re-peel.
+// Returns the status (or POOL_FULL, with the view unchanged); *bits = (u in C) | (v in C) << 1.
+__device__ int process_update(const ServeArgs &A, TargetDev &S, int op, int32_t x, int32_t y, int32_t ep,
+                              int *bits) {
+    const int st = apply_update(A, S, op, x, y);
+    if (st == POOL_FULL) return st;
     if (st == ABCORE_OK) {
         const bool mx = S.M[x], my = S.M[y];
         __syncthreads();
@@ -518,6 +554,15 @@ __global__ void __launch_bounds__(SERVE_THREADS) k_serve(ServeArgs A) {
         ep += 2;
         int bits = 0;
         const int st = process_update(A, S, r.op, x, y, ep, &bits);
+        if (st == POOL_FULL) {
+            // hold request k back: the loop closes at k for every block, the host grows this
+            // target's pool and relaunches, and k is processed then (its answer is unchanged)
+            if (threadIdx.x == 0) {
+                A.grow[t] = 1;
+                atomicMin(A.exit_at, k);
+            }
+            break;
+        }
         if (threadIdx.x == 0) {
             // component labels (kept by the first target's block): an insert joins the two
             // components; a delete may split one, which the next label request recomputes
@@ -630,6 +675,107 @@ __global__ void k_cc_inserted(int32_t nU, TargetDev S, int32_t *parent) {
     }
 }
 
+// ---- GFQ with the paper's scope (Section 5): after an update, the connected components of its
+// endpoints are peeled again from scratch on the current graph (an ablation of the certificate
+// scope above; both give the exact core of the updated graph). One view of the updates (no core
+// state: each query re-peels), the component forest, and a level-synchronous peel over the
+// component(s), a warp per frontier vertex.
+
+// The update's edge change on the view; ids[0], ids[1] receive the endpoints' internal ids.
+__global__ void __launch_bounds__(SERVE_THREADS) k_gfq_apply(ServeArgs A, TargetDev V, int op, int32_t u, int32_t v,
+                                                             int32_t *ids, int *status) {
+    const int32_t x = __ldg(&A.old2new[u]);
+    const int32_t y = __ldg(&A.old2new[A.nU + v]);
+    const int st = apply_update(A, V, op, x, y);
+    if (threadIdx.x == 0) {
+        ids[0] = x;
+        ids[1] = y;
+        *status = st;
+    }
+}
+
+// An insert unites the endpoints' components.
+__global__ void k_gfq_unite(int32_t *parent, const int32_t *ids) { abc::cc_unite(parent, ids[0], ids[1]); }
+
+// Before a delete is accounted for: keep[x] = 1 for the vertices of the endpoints' component.
+__global__ void k_gfq_mark(int32_t *parent, int64_t n, const int32_t *ids, uint8_t *keep) {
+    const int32_t r = abc::cc_find(parent, ids[0]);
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        keep[x] = abc::cc_find(parent, (int32_t)x) == r ? 1 : 0;
+}
+
+// ... then that component's forest is reset, to be rebuilt from its remaining edges.
+__global__ void k_gfq_reset(int32_t *parent, int64_t n, const uint8_t *keep) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        if (keep[x]) parent[x] = (int32_t)x;
+}
+
+// Inserted edges of kept vertices (each seen from its U endpoint) rejoin the forest.
+__global__ void k_gfq_hook_inserted(int32_t nU, TargetDev V, int32_t *parent, const uint8_t *keep) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nU; x += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[x]) continue;
+        const int2 seg = V.ins[x];
+        for (int32_t i = 0; i < seg.y; ++i) {
+            const int32_t z = V.pool[seg.x + i];
+            if (z >= 0) abc::cc_unite(parent, (int32_t)x, z);
+        }
+    }
+}
+
+// Start of the re-peel: vertices of the endpoints' components get their current degree as count;
+// those below their bound form the first frontier. Everything else is outside the scope.
+__global__ void k_gfq_init(int32_t *parent, int64_t n, int32_t nU, const int32_t *ids, int32_t alpha, int32_t beta,
+                           const int32_t *deg, int32_t *cnt, uint8_t *alive, int32_t *front, unsigned *nfront,
+                           unsigned long long *scope) {
+    const int32_t ru = abc::cc_find(parent, ids[0]), rv = abc::cc_find(parent, ids[1]);
+    unsigned long long k = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = abc::cc_find(parent, (int32_t)x);
+        if (r != ru && r != rv) {
+            alive[x] = 0;
+            continue;
+        }
+        ++k;
+        const int32_t d = deg[x];
+        cnt[x] = d;
+        if (d >= (x < nU ? alpha : beta)) {
+            alive[x] = 1;
+        } else {
+            alive[x] = 0;
+            front[atomicAdd(nfront, 1u)] = (int32_t)x;
+        }
+    }
+    k = (unsigned long long)abc::warp_sum64((long long)k);
+    if ((threadIdx.x & 31) == 0 && k) atomicAdd(scope, k);
+}
+
+// One peel round over the view: each removed vertex lowers its live neighbours' counts; the
+// decrement that crosses a bound removes the neighbour (exactly once) into the next frontier.
+__global__ void k_gfq_round(ServeArgs A, TargetDev V, int32_t alpha, int32_t beta, int32_t *cnt, uint8_t *alive,
+                            const int32_t *fin, unsigned nin, int32_t *fout, unsigned *nout) {
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < nin; i += nw) {
+        const int32_t w = fin[i];
+        for_neighbours(A, V, w, [&](int32_t z) {
+            if (!alive[z]) return;
+            const int old = atomicSub(&cnt[z], 1);
+            if (old == (z < A.nU ? alpha : beta)) {
+                alive[z] = 0;
+                fout[atomicAdd(nout, 1u)] = z;
+            }
+        });
+    }
+}
+
+// Current degree of every vertex of the base graph (the view starts empty).
+__global__ void k_gfq_deg(const int64_t *off, int64_t n, int32_t *deg, int2 *ins) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        deg[x] = (int32_t)(off[x + 1] - off[x]);
+        ins[x] = make_int2(-1, 0);
+    }
+}
+
 }  // namespace
 
 struct ServeState {
@@ -648,6 +794,8 @@ struct ServeState {
     unsigned long long *d_resp_seq = nullptr, *d_ctl = nullptr;
     unsigned long long *d_progress = nullptr, *d_exit_at = nullptr;
     int *d_err = nullptr;
+    int *d_grow = nullptr;              // per target: its pool must grow before it can go on
+    int64_t pool_grows = 0;
     int32_t *d_comp = nullptr;          // component union-find (see k_serve)
     int *d_comp_stale = nullptr;
     unsigned long long next_seq = 0, consumed = 0;
@@ -698,6 +846,7 @@ static int launch_loop(abcore_ctx *ctx, ServeState *s) {
     A.progress_dev = s->d_progress;
     A.exit_at = s->d_exit_at;
     A.err = s->d_err;
+    A.grow = s->d_grow;
     A.comp = s->d_comp;
     A.comp_stale = s->d_comp_stale;
     A.slots = s->slots;
@@ -717,8 +866,47 @@ static int check_device_error(abcore_ctx *ctx, ServeState *s) {
     if (s->loop_launched && !loop_running(s)) {
         int e = 0;
         ABC_CU(cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e == ABCORE_ENOMEM) return ctx->fail(ABCORE_ENOMEM, "serve: inserted-edge pool exhausted");
+        if (e == ABCORE_ENOMEM) return ctx->fail(ABCORE_ENOMEM, "serve: certificate level limit reached");
         if (e) return ctx->fail(e, "serve: device reported error %d", e);
+    }
+    return ABCORE_OK;
+}
+
+// Grow the inserted-edge pool of every target whose loop block stopped for lack of room (the
+// loop has finished): a pool of twice the entries, the used prefix copied over. If the device
+// has no memory for it, the call reports ABCORE_ENOMEM and the target's requests keep waiting;
+// a later call tries again.
+static int grow_pools(abcore_ctx *ctx, ServeState *s) {
+    const int nt = (int)s->tdev.size();
+    std::vector<int> want(nt, 0);
+    ABC_CU(cudaMemcpyAsync(want.data(), s->d_grow, sizeof(int) * nt, cudaMemcpyDeviceToHost, s->stream));
+    ABC_CU(cudaStreamSynchronize(s->stream));
+    for (int t = 0; t < nt; ++t) {
+        if (!want[t]) continue;
+        TargetDev &T = s->tdev[t];
+        int32_t top = 0;
+        ABC_CU(cudaMemcpyAsync(&top, T.pool_top, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+        ABC_CU(cudaStreamSynchronize(s->stream));
+        const int64_t ncap = std::min<int64_t>(2 * (int64_t)T.pool_cap, INT32_MAX);
+        if (ncap <= T.pool_cap)
+            return ctx->fail(ABCORE_ENOMEM, "serve: target %d's inserted-edge pool is at its 2^31-entry limit", t);
+        int32_t *np = nullptr;
+        const int rc = ctx->alloc(&np, (size_t)ncap, "serve inserted pool");
+        if (rc) return ctx->fail(rc, "serve: target %d's inserted-edge pool cannot grow to %lld entries; its "
+                                     "requests wait until device memory frees up", t, (long long)ncap);
+        ABC_CU(cudaMemcpyAsync(np, T.pool, sizeof(int32_t) * (size_t)std::max(top, 0), cudaMemcpyDeviceToDevice,
+                               s->stream));
+        ABC_CU(cudaStreamSynchronize(s->stream));
+        for (auto &b : s->bufs)
+            if (b == (void *)T.pool) b = (void *)np;
+        ctx->release(T.pool);
+        T.pool = np;
+        T.pool_cap = (int32_t)ncap;
+        ABC_CU(cudaMemcpyAsync(s->d_targets + t, &T, sizeof(TargetDev), cudaMemcpyHostToDevice, s->stream));
+        want[t] = 0;
+        ABC_CU(cudaMemcpyAsync(s->d_grow + t, &want[t], sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        ABC_CU(cudaStreamSynchronize(s->stream));
+        s->pool_grows++;
     }
     return ABCORE_OK;
 }
@@ -726,6 +914,7 @@ static int check_device_error(abcore_ctx *ctx, ServeState *s) {
 static int ensure_loop(abcore_ctx *ctx, ServeState *s) {
     if (s->next_seq > min_progress(s) && !loop_running(s)) {
         ABC_TRY(check_device_error(ctx, s));
+        if (s->loop_launched) ABC_TRY(grow_pools(ctx, s));
         ABC_TRY(launch_loop(ctx, s));
     }
     return ABCORE_OK;
@@ -742,6 +931,7 @@ static void release_serve(abcore_ctx *ctx, ServeState *s) {
     ctx->release(s->d_progress);
     ctx->release(s->d_exit_at);
     ctx->release(s->d_err);
+    ctx->release(s->d_grow);
     ctx->release(s->d_comp);
     ctx->release(s->d_comp_stale);
     if (s->h_req) cudaFreeHost(s->h_req);
@@ -759,13 +949,30 @@ static void release_serve(abcore_ctx *ctx, ServeState *s) {
     s->loop_launched = false;
 }
 
-// Rebuild the CSR from the current graph (target 0's view) after updates, so static calls and
-// new targets see the updated graph.
-static int materialize(abcore_ctx *ctx) {
-    ServeState *s = ctx->serve;
-    if (!s || !s->dirty || s->tdev.empty()) return ABCORE_OK;
+// State of on-the-fly queries with the component scope (query_scope = 1): one view of the updates
+// (the TargetDev fields tomb, ins, pool, pool_top, pool_cap and deg; the rest unused), the
+// component forest of the current graph, and the re-peel's counts, flags and frontiers.
+struct GfqState {
+    TargetDev V{};
+    int32_t *parent = nullptr;   // [n] union-find forest over the current graph
+    int32_t *cnt = nullptr;      // [n] re-peel counts
+    uint8_t *alive = nullptr;    // [n] re-peel membership (0 outside the scope)
+    uint8_t *keep = nullptr;     // [n] the component a delete cuts
+    int32_t *front = nullptr;    // [2n] two frontiers
+    unsigned *nfront = nullptr;  // [2]
+    int32_t *ids = nullptr;      // [2] the update's internal endpoint ids
+    int *status = nullptr;
+    unsigned long long *scope = nullptr;  // vertices re-peeled (accumulated)
+    std::vector<void *> bufs;
+    bool dirty = false;
+};
+
+// Rebuild the CSR from a view of the updated graph, after `drop` has released the state that
+// owns the view (the view's buffers stay valid until the edges are collected), so static calls
+// and new targets see the updated graph.
+static int rebuild_from_view(abcore_ctx *ctx, const TargetDev &view, void (*drop)(abcore_ctx *)) {
     const Graph &g = ctx->g;
-    const int64_t cap = g.m + s->pool_cap / 2 + 16;  // every inserted edge holds two pool entries
+    const int64_t cap = g.m + view.pool_cap / 2 + 16;  // an inserted edge holds two pool entries
     int32_t *eu = nullptr, *ev = nullptr;
     unsigned long long *cnt = nullptr;
     ABC_TRY(ctx->alloc(&eu, (size_t)cap, "rebuild edges"));
@@ -774,16 +981,14 @@ static int materialize(abcore_ctx *ctx) {
     unsigned long long m2 = 0;
     if (!rc) {
         cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream);
-        k_collect_edges<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, g.adj, g.new2old, g.nU, s->tdev[0], eu, ev, cnt);
+        k_collect_edges<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(g.off, g.adj, g.new2old, g.nU, view, eu, ev, cnt);
         cudaMemcpyAsync(&m2, cnt, sizeof(m2), cudaMemcpyDeviceToHost, ctx->stream);
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) rc = ctx->cuda_fail(e, "rebuild");
     }
     const int32_t nU = g.nU, nV = g.nV;
     if (!rc) {
-        release_serve(ctx, s);
-        delete s;
-        ctx->serve = nullptr;
+        drop(ctx);
         free_batch(ctx);
         free_peel(ctx);
         rc = build_graph_from_device_edges(ctx, nU, nV, (int64_t)m2, eu, ev);
@@ -794,9 +999,27 @@ static int materialize(abcore_ctx *ctx) {
     return rc;
 }
 
+static void drop_serve(abcore_ctx *ctx) {
+    release_serve(ctx, ctx->serve);
+    delete ctx->serve;
+    ctx->serve = nullptr;
+}
+
 int serve_materialize(abcore_ctx *ctx) {
     if (ctx->serve && ctx->serve->loop_launched) ABC_TRY(serve_stop(ctx));  // finish outstanding requests
-    return materialize(ctx);
+    if (ctx->serve && ctx->serve->dirty && !ctx->serve->tdev.empty())
+        ABC_TRY(rebuild_from_view(ctx, ctx->serve->tdev[0], drop_serve));
+    if (ctx->gfq && ctx->gfq->dirty) ABC_TRY(rebuild_from_view(ctx, ctx->gfq->V, free_gfq));
+    return ABCORE_OK;
+}
+
+void free_gfq(abcore_ctx *ctx) {
+    GfqState *q = ctx->gfq;
+    if (!q) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (void *p : q->bufs) ctx->release(p);
+    delete q;
+    ctx->gfq = nullptr;
 }
 
 void free_serve(abcore_ctx *ctx) {
@@ -814,11 +1037,9 @@ static int serve_alloc(abcore_ctx *ctx, ServeState *s, T **p, size_t n, const ch
 }
 
 int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t nt, int32_t slots) {
-    if (ctx->serve) {
-        ABC_TRY(serve_stop(ctx));
-        ABC_TRY(materialize(ctx));
-        free_serve(ctx);
-    }
+    ABC_TRY(serve_materialize(ctx));  // served or queried updates become the CSR
+    free_serve(ctx);
+    free_gfq(ctx);
     const Graph &g = ctx->g;
     const int64_t n = g.n();
     ServeState *s = new ServeState();
@@ -844,6 +1065,8 @@ int serve_start(abcore_ctx *ctx, const int32_t *ta, const int32_t *tb, int32_t n
     ABC_CU(cudaHostGetDevicePointer((void **)&s->d_ctl, s->h_ctl, 0));
     ABC_TRY(ctx->alloc(&s->d_progress, nt, "serve progress"));
     ABC_TRY(ctx->alloc(&s->d_err, 1, "serve error"));
+    ABC_TRY(ctx->alloc(&s->d_grow, nt, "serve pool growth"));
+    ABC_CU(cudaMemsetAsync(s->d_grow, 0, sizeof(int) * nt, ctx->stream));
     ABC_TRY(ctx->alloc(&s->d_exit_at, 1, "serve exit"));
     ABC_CU(cudaMemsetAsync(s->d_progress, 0, sizeof(unsigned long long) * nt, ctx->stream));
     ABC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), ctx->stream));
@@ -972,7 +1195,160 @@ int serve_stop(abcore_ctx *ctx) {
     return check_device_error(ctx, s);
 }
 
+template <class T>
+static int gfq_alloc(abcore_ctx *ctx, GfqState *q, T **p, size_t n, const char *what) {
+    ABC_TRY(ctx->alloc(p, n, what));
+    q->bufs.push_back((void *)*p);
+    return ABCORE_OK;
+}
+
+// The component-scoped query state on the current CSR: an empty view and the component forest
+// (GFQ's preprocessing).
+static int gfq_prepare(abcore_ctx *ctx) {
+    if (ctx->gfq) return ABCORE_OK;
+    ABC_TRY(serve_materialize(ctx));
+    free_serve(ctx);
+    const Graph &g = ctx->g;
+    const int64_t n = std::max<int64_t>(g.n(), 1);
+    GfqState *q = new GfqState();
+    ctx->gfq = q;
+    TargetDev &V = q->V;
+    const int64_t tomb_words = (2 * g.m + 31) / 32 + 1;
+    V.pool_cap = (int32_t)std::min<int64_t>(8 * ctx->prm.serve_inserts + 1024, INT32_MAX);
+    ABC_TRY(gfq_alloc(ctx, q, &V.tomb, (size_t)tomb_words, "query tombstones"));
+    ABC_TRY(gfq_alloc(ctx, q, &V.ins, (size_t)n, "query inserted segments"));
+    ABC_TRY(gfq_alloc(ctx, q, &V.pool, (size_t)V.pool_cap, "query inserted pool"));
+    ABC_TRY(gfq_alloc(ctx, q, &V.pool_top, 1, "query inserted pool"));
+    ABC_TRY(gfq_alloc(ctx, q, &V.deg, (size_t)n, "query degrees"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->parent, (size_t)n, "query components"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->cnt, (size_t)n, "query counts"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->alive, (size_t)n, "query membership"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->keep, (size_t)n, "query cut component"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->front, (size_t)(2 * n), "query frontiers"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->nfront, 2, "query frontier sizes"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->ids, 2, "query endpoints"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->status, 1, "query status"));
+    ABC_TRY(gfq_alloc(ctx, q, &q->scope, 1, "query scope size"));
+    ABC_CU(cudaMemsetAsync(V.tomb, 0, sizeof(uint32_t) * tomb_words, ctx->stream));
+    ABC_CU(cudaMemsetAsync(V.pool_top, 0, sizeof(int32_t), ctx->stream));
+    const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((g.n() + 255) / 256, (int64_t)ctx->num_sms * 16));
+    if (g.n() > 0) k_gfq_deg<<<gi, 256, 0, ctx->stream>>>(g.off, g.n(), V.deg, V.ins);
+    ctx->stats.launches++;
+    ABC_TRY(cc_hook_base(ctx, q->parent, nullptr, ctx->stream));
+    ABC_CU(cudaGetLastError());
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    return ABCORE_OK;
+}
+
+// Double the view's inserted-edge pool (its used prefix copied over).
+static int gfq_grow(abcore_ctx *ctx, GfqState *q) {
+    TargetDev &V = q->V;
+    int32_t top = 0;
+    ABC_CU(cudaMemcpyAsync(&top, V.pool_top, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    const int64_t ncap = std::min<int64_t>(2 * (int64_t)V.pool_cap, INT32_MAX);
+    if (ncap <= V.pool_cap) return ctx->fail(ABCORE_ENOMEM, "query: the inserted-edge pool is at its 2^31-entry limit");
+    int32_t *np = nullptr;
+    ABC_TRY(ctx->alloc(&np, (size_t)ncap, "query inserted pool"));
+    ABC_CU(cudaMemcpyAsync(np, V.pool, sizeof(int32_t) * (size_t)std::max(top, 0), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    for (auto &b : q->bufs)
+        if (b == (void *)V.pool) b = (void *)np;
+    ctx->release(V.pool);
+    V.pool = np;
+    V.pool_cap = (int32_t)ncap;
+    return ABCORE_OK;
+}
+
+// GFQ (Section 5) with the paper's scope: apply the update, keep the component forest current
+// (an insert unites; a delete re-runs the affected component's components), then re-peel the
+// endpoints' components from scratch with a level-synchronous peel over the current graph.
+static int gfq_query(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta, uint8_t *in_core) {
+    ABC_TRY(gfq_prepare(ctx));
+    GfqState *q = ctx->gfq;
+    const Graph &g = ctx->g;
+    const int64_t n = g.n();
+    ServeArgs A{};
+    A.off = g.off;
+    A.adj = g.adj;
+    A.old2new = g.old2new;
+    A.nU = g.nU;
+    A.nV = g.nV;
+    A.err = q->status;  // (apply_update reports a pool fault here; pool_room rules it out)
+    int st = POOL_FULL;
+    while (st == POOL_FULL) {
+        k_gfq_apply<<<1, SERVE_THREADS, 0, ctx->stream>>>(A, q->V, op, u, v, q->ids, q->status);
+        ctx->stats.launches++;
+        ABC_CU(cudaGetLastError());
+        ABC_CU(cudaMemcpyAsync(&st, q->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        ABC_CU(cudaStreamSynchronize(ctx->stream));
+        if (st == POOL_FULL) ABC_TRY(gfq_grow(ctx, q));
+    }
+    if (st != ABCORE_OK && st != ABCORE_EEXIST && st != ABCORE_ENOENT)
+        return ctx->fail(st, "query: device reported error %d", st);
+    const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16));
+    if (st == ABCORE_OK) {
+        q->dirty = true;
+        if (op == ABCORE_INSERT) {
+            k_gfq_unite<<<1, 1, 0, ctx->stream>>>(q->parent, q->ids);
+            ctx->stats.launches++;
+        } else {
+            k_gfq_mark<<<gi, 256, 0, ctx->stream>>>(q->parent, n, q->ids, q->keep);
+            k_gfq_reset<<<gi, 256, 0, ctx->stream>>>(q->parent, n, q->keep);
+            ctx->stats.launches += 2;
+            ABC_TRY(cc_hook_rows(ctx, q->parent, q->V.tomb, ctx->stream, q->keep));
+            if (g.nU > 0) k_gfq_hook_inserted<<<gi, 256, 0, ctx->stream>>>(g.nU, q->V, q->parent, q->keep);
+            ctx->stats.launches++;
+        }
+    }
+    // the re-peel of the endpoints' components
+    unsigned h[2] = {0, 0};
+    unsigned long long before = 0, after = 0;
+    ABC_CU(cudaMemcpyAsync(&before, q->scope, sizeof(before), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaMemsetAsync(q->nfront, 0, 2 * sizeof(unsigned), ctx->stream));
+    int32_t *fa = q->front, *fb = q->front + std::max<int64_t>(n, 1);
+    k_gfq_init<<<gi, 256, 0, ctx->stream>>>(q->parent, n, g.nU, q->ids, alpha, beta, q->V.deg, q->cnt, q->alive, fa,
+                                            q->nfront, q->scope);
+    ctx->stats.launches++;
+    ABC_CU(cudaGetLastError());
+    ABC_CU(cudaMemcpyAsync(&h[0], q->nfront, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaMemcpyAsync(&after, q->scope, sizeof(after), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    while (h[0] > 0) {
+        ABC_CU(cudaMemsetAsync(q->nfront + 1, 0, sizeof(unsigned), ctx->stream));
+        const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)h[0] * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+        k_gfq_round<<<std::max(blocks, 1u), 256, 0, ctx->stream>>>(A, q->V, alpha, beta, q->cnt, q->alive, fa, h[0], fb,
+                                                                    q->nfront + 1);
+        ctx->stats.launches++;
+        ABC_CU(cudaGetLastError());
+        ABC_CU(cudaMemcpyAsync(&h[1], q->nfront + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+        ABC_CU(cudaStreamSynchronize(ctx->stream));
+        std::swap(fa, fb);
+        h[0] = h[1];
+    }
+    int32_t ids[2] = {0, 0};
+    uint8_t a2[2] = {0, 0};
+    ABC_CU(cudaMemcpyAsync(ids, q->ids, sizeof(ids), cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    ABC_CU(cudaMemcpyAsync(&a2[0], q->alive + ids[0], 1, cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaMemcpyAsync(&a2[1], q->alive + ids[1], 1, cudaMemcpyDeviceToHost, ctx->stream));
+    ABC_CU(cudaStreamSynchronize(ctx->stream));
+    *in_core = (a2[0] && a2[1]) ? 1 : 0;
+    ctx->stats.scope_queries++;
+    ctx->stats.scope_vertices += (int64_t)(after - before);
+    if (st != ABCORE_OK)
+        return ctx->fail(st, st == ABCORE_EEXIST ? "insert: edge already present" : "delete: edge not present");
+    return ABCORE_OK;
+}
+
 int query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta, uint8_t *in_core) {
+    if (ctx->prm.query_scope == 1) return gfq_query(ctx, u, v, op, alpha, beta, in_core);
+    if (ctx->gfq) {
+        // updates queried with the component scope become the CSR the serving loop starts from
+        ABC_TRY(serve_materialize(ctx));
+        free_gfq(ctx);
+    }
     ServeState *s = ctx->serve;
     int32_t t = -1;
     if (s)

@@ -63,9 +63,9 @@ def test_batch_full_size_20Mx10M_500M_vs_oracle():
             if not (np.array_equal(plain[p][0], want[p][0]) and np.array_equal(plain[p][1], want[p][1]))]
     assert not bad, "batch masks differ from the oracle at %s" % bad
     assert not badp, "plain masks differ from the oracle at %s" % badp
-    # the sample is not degenerate: some cores are empty, some hold most of the graph
+    # the sample is not degenerate: some cores are tiny, some hold most of the graph
     sizes = [int(want[p][0].sum()) + int(want[p][1].sum()) for p in sample]
-    assert min(sizes) == 0 and max(sizes) > (nU + nV) // 4
+    assert min(sizes) < (nU + nV) // 100 and max(sizes) > (nU + nV) // 4
 
 
 def test_serve_full_size_10Mx5M_200M_stream_vs_oracle_replay():

@@ -206,46 +206,113 @@ def test_serve_rejects_bad_requests():
     core.close()
 
 
-def test_inserted_edge_pool_exhaustion_is_reported():
-    # a tiny inserted-edge pool: the loop stops with ABCORE_ENOMEM (a status, not a fault) and
-    # the library stays usable afterwards
-    import time
-    nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
+def test_small_inserted_edge_pool_grows_and_answers_stay_exact():
+    # a tiny inserted-edge pool (16 inserts' worth per target): inserts that do not fit are held
+    # back until the library has grown the pool, so the whole stream -- thousands of inserts,
+    # deletes of inserted edges among them -- finishes with every answer equal to the oracle's
+    spec = synth.WORKLOADS["serve-10kx5k-200k"]
+    nU, nV, eu, ev = synth.make_graph(spec)
     eu, ev = eu.numpy(), ev.numpy()
+    stream = synth.edge_update_stream(eu, ev, nU, nV, 6000, 11)
+    targets = spec["targets"]
+    ans, bits, status = _oracle(nU, nV, eu, ev, stream, targets)
     core = ABCore(0)
     core.load_edges(nU, nV, eu, ev)
     core.set_param("serve_inserts", 16)
-    core.serve_start([(2, 2)], ring_slots=64)
-    present = set(zip(eu.tolist(), ev.tolist()))
-    rng = np.random.default_rng(1)
-    ins = []
-    while len(ins) < 2000:
-        u, v = int(rng.integers(nU)), int(rng.integers(nV))
-        if (u, v) not in present:
-            present.add((u, v))
-            ins.append((u, v))
-    err = None
-    t0 = time.time()
-    k = 0
-    try:
-        while k < len(ins):
-            assert time.time() - t0 < 60
-            hi = min(len(ins), k + 32)
-            arr = (abi.abcore_req * (hi - k))()
-            for i, (u, v) in enumerate(ins[k:hi]):
-                arr[i].op, arr[i].u, arr[i].v, arr[i].target, arr[i].tag = abi.ABCORE_INSERT, u, v, 0, k + i
-            if core.serve_submit(arr) is not None:
-                k = hi
-            core.serve_poll(4096)
-        core.serve_stop()
-    except ABCoreError as e:
-        err = e
-    assert err is not None and err.code == abi.ABCORE_ENOMEM
+    out = _serve(core, stream, targets, batch=64, ring=128)
+    assert np.array_equal(np.array([r.status for r in out]), status)
+    assert np.array_equal(np.array([r.in_core for r in out]), ans)
+    assert np.array_equal(np.array([r.u_in | (r.v_in << 1) for r in out]), bits)
+    assert int((stream.op == 0).sum()) > 16 * 4 * 8  # far more inserts than the first pools held
+    # the served graph is the oracle's final graph
+    mu, mv = core.compute(5, 5)
+    fin = {}
+    for k in range(len(stream)):
+        key = (int(stream.u[k]), int(stream.v[k]))
+        fin[key] = stream.op[k] == 0
+    cur = set(zip(eu.tolist(), ev.tolist()))
+    for key, present in fin.items():
+        (cur.add if present else cur.discard)(key)
+    fu = np.array([e[0] for e in cur], dtype=np.int32)
+    fv = np.array([e[1] for e in cur], dtype=np.int32)
+    off, adj = oracle.build_csr(nU, nV, fu, fv)
+    wu, wv = oracle.peel(nU, nV, off, adj, 5, 5)
+    assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv)
+    core.close()
+
+
+def _query_all(core, stream, targets):
+    return np.array([core.query_edge(int(stream.u[k]), int(stream.v[k]), int(stream.op[k]),
+                                     targets[int(stream.target[k])][0], targets[int(stream.target[k])][1])
+                     for k in range(len(stream))], dtype=np.int8)
+
+
+def test_component_scope_matches_oracle_and_certificate_scope():
+    # the paper's GFQ scope (the endpoints' components re-peeled from scratch) against the oracle
+    # at every step and against the certificate scope of the serving loop
+    spec = synth.WORKLOADS["serve-10kx5k-200k"]
+    nU, nV, eu, ev = synth.make_graph(spec)
+    eu, ev = eu.numpy(), ev.numpy()
+    stream = synth.edge_update_stream(eu, ev, nU, nV, 1500, 5)
+    targets = spec["targets"]
+    ans, _, _ = _oracle(nU, nV, eu, ev, stream, targets)
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    core.set_param("query_scope", 1)
+    got = _query_all(core, stream, targets)
+    st = core.stats()
+    assert np.array_equal(got, ans)
+    assert st["scope_queries"] == len(stream) and st["scope_vertices"] > 0
     core.close()
     core = ABCore(0)
     core.load_edges(nU, nV, eu, ev)
-    mu, mv = core.compute(2, 3)
-    off, adj = oracle.build_csr(nU, nV, eu, ev)
-    wu, wv = oracle.peel(nU, nV, off, adj, 2, 3)
-    assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv)
+    out = _serve(core, stream, targets, batch=128)
+    assert np.array_equal(np.array([r.in_core for r in out], dtype=np.int8), got)
+    core.close()
+
+
+def test_component_scope_on_many_components_merging_and_splitting():
+    # four disjoint random blocks: inserts bridge blocks (components merge), deletes cut bridges
+    # and block edges (components split); the forest and the scoped re-peel must follow
+    rng = np.random.default_rng(9)
+    nb, bu, bv = 4, 30, 20
+    nU, nV = nb * bu, nb * bv
+    edges = set()
+    for b in range(nb):
+        while len(edges) < (b + 1) * 180:
+            edges.add((b * bu + int(rng.integers(bu)), b * bv + int(rng.integers(bv))))
+    base = sorted(edges)
+    eu = np.array([e[0] for e in base], dtype=np.int32)
+    ev = np.array([e[1] for e in base], dtype=np.int32)
+    cur = list(base)
+    ops, us, vs, tg = [], [], [], []
+    present = set(base)
+    for k in range(700):
+        if rng.random() < 0.55:
+            while True:
+                u, v = int(rng.integers(nU)), int(rng.integers(nV))
+                if (u, v) not in present:
+                    break
+            present.add((u, v)); cur.append((u, v)); ops.append(0)
+        else:
+            i = int(rng.integers(len(cur)))
+            u, v = cur[i]
+            cur[i] = cur[-1]; cur.pop(); present.discard((u, v)); ops.append(1)
+        us.append(u); vs.append(v); tg.append(int(rng.integers(3)))
+    stream = synth.StreamOp(op=np.array(ops, np.int8), u=np.array(us, np.int32), v=np.array(vs, np.int32),
+                            target=np.array(tg, np.int8), t_unit=np.arange(len(ops), dtype=np.float64))
+    targets = [(2, 2), (3, 4), (5, 3)]
+    ans, _, _ = _oracle(nU, nV, eu, ev, stream, targets)
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    core.set_param("query_scope", 1)
+    got = _query_all(core, stream, targets)
+    assert np.array_equal(got, ans)
+    # the forest after all updates names the oracle's components of the final graph
+    lu, lv, ncomp = core.components()
+    fu = np.array([e[0] for e in cur], dtype=np.int32)
+    fv = np.array([e[1] for e in cur], dtype=np.int32)
+    off, adj = oracle.build_csr(nU, nV, fu, fv)
+    lab, nc = oracle.components(nU, nV, off, adj)
+    assert ncomp == nc and np.array_equal(np.concatenate([lu.cpu().numpy(), lv.cpu().numpy()]), lab)
     core.close()
