@@ -834,6 +834,29 @@ def run_serve(args, rank, world, local):
         parity = ("%d/%d sampled updates (both kinds, every target, spread over the stream) answer as the oracle's "
                   "replay of the stream up to them (%.0f s, %d threads); answers identical across rates: %s"
                   % (ok, len(ks), time.perf_counter() - t, oracle_threads(), same))
+    # the paper's GFQ scope as an ablation: the first updates of the same stream, each answered by
+    # re-peeling the endpoints' components from scratch (query_scope = 1), one call at a time
+    n_scope = min(n_ops, args.scope_ops)
+    scope = None
+    if n_scope > 0:
+        core = ABCore(local)
+        core.load_edges(nU, nV, eu, ev)
+        core.set_param("query_scope", 1)
+        lat, got = [], []
+        for k in range(n_scope):
+            tg = targets[int(stream.target[k])]
+            t = time.perf_counter()
+            got.append(core.query_edge(int(stream.u[k]), int(stream.v[k]), int(stream.op[k]), tg[0], tg[1]))
+            lat.append((time.perf_counter() - t) * 1e3)
+        st = core.stats()
+        core.close()
+        first = answers[spec["rates"][0]]
+        scope = {"updates": n_scope, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                 "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(np.mean(lat)), 3),
+                 "queries_per_s": round(n_scope / (sum(lat) / 1e3), 1),
+                 "vertices_repeeled_per_query": round(st["scope_vertices"] / max(st["scope_queries"], 1)),
+                 "answers_identical_to_certificate_scope": got == list(first[:n_scope]),
+                 "note": "one abcore_query_edge call per update, closed loop (latency is the call's wall time)"}
     # component labels (the GFQ preprocessing) on the base graph, timed on the device
     core = ABCore(local)
     core.load_edges(nU, nV, eu, ev)
@@ -875,6 +898,7 @@ def run_serve(args, rank, world, local):
                    "targets": [list(t) for t in targets], "stream_gen_s": round(gen_s, 2),
                    "parallelism": "single"},
         "rates": results, "answers_identical_across_rates": same, "parity": parity, "cpu_baseline": cpu,
+        "component_scope": scope,
         "components": comps,
         "plain_full_peel_per_query_qps": round(plain_qps, 1), "clocks": clk,
         "e2e": {"value": top["p99_ms"], "unit": "ms", "h2d_bytes_per_step": n_ops * req_size,
@@ -1024,6 +1048,8 @@ def main():
     ap.add_argument("--no-gccplus", action="store_true", help="skip the GCC+ (core-number pruned) leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched grid beside the single peel")
     ap.add_argument("--serve-ops", type=int, default=0, help="updates per rate (default: the workload's)")
+    ap.add_argument("--scope-ops", type=int, default=300,
+                    help="serving: updates also answered with the paper's component scope (0: skip)")
     ap.add_argument("--param", action="append", default=[], help="library parameter name=value (repeatable)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -514,6 +514,15 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         if (value < 0 || value > 32) return ctx->fail(ABCORE_EINVAL, "batch_wave must be 0..32");
         p.batch_wave = (int)value;
         free_batch(ctx);
+    } else if (k == "batch_plain_below") {
+        if (value < 0 || value > INT32_MAX) return ctx->fail(ABCORE_EINVAL, "batch_plain_below must be >= 0");
+        ABC_TRY(abcore_sync(ctx));
+        p.batch_plain_below = (int)value;
+        free_batch(ctx);
+    } else if (k == "batch_seed") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "batch_seed must be 0 or 1");
+        p.batch_seed = (int)value;
+        free_batch(ctx);
     } else if (k == "hub_degree") {
         if (value < 0) return ctx->fail(ABCORE_EINVAL, "hub_degree must be >= 0");
         ABC_TRY(abcore_sync(ctx));
@@ -578,6 +587,8 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "serve_inserts") *value = p.serve_inserts;
     else if (k == "algo") *value = p.algo;
     else if (k == "query_scope") *value = p.query_scope;
+    else if (k == "batch_seed") *value = p.batch_seed;
+    else if (k == "batch_plain_below") *value = p.batch_plain_below;
     else if (k == "log_level") *value = p.log_level;
     else return ctx->fail(ABCORE_EINVAL, "unknown parameter '%s'", name);
     return ABCORE_OK;

@@ -43,6 +43,8 @@ struct ChainDev {
     int32_t hubcutU, hubcutV;
     int32_t first_block, nblocks;
     int32_t col;             // column of this chain in lvl
+    int32_t seed_col;        // column of a finished chain with a smaller alpha and the same betas
+                             // (its step-j core contains this chain's), or -1
     int64_t sa, ea, sb, eb;  // step-0 violator slices (see stream_range)
 };
 
@@ -61,6 +63,9 @@ struct BatchArgs {
     const ChainDev *chains;
     const ChainMem *mem;
     const int32_t *betas;
+    const int32_t *pvs;      // per beta: the V candidate prefix (vertices of degree >= beta)
+    const float *fracs;      // per beta: the share of a U row's step-0 candidate entries below it
+                             // (where the search for a fallen U row's new end starts)
     int32_t nchains;
     uint8_t *lvl;
     int32_t lvl_stride;
@@ -112,6 +117,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     a.lvl = B.lvl;
     a.lvl_stride = B.lvl_stride;
     a.lvl_col = cd.col;
+    a.seed_col = cd.seed_col;
+    a.dead_own = cd.seed_col >= 0 ? 1 : 0;
     a.step = 0;
     a.flags = B.flags;
     a.flag_first = cd.first_block;
@@ -146,25 +153,30 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     if (prof) prof[1] = abc::now_ns();
     for (int j = 1; j < cd.nsteps; ++j) {
         const int32_t prev = a.thrV;
+        const int32_t pv_prev = a.pV;
         a.thrV = B.betas[cd.beta_off + j];
         a.step = j;
         a.epoch = (uint32_t)j + 1;
-        // V vertices alive after step j-1 (count >= previous bound) that miss the new bound
-        int pc = 0;
-        for (int64_t b = t0 - (threadIdx.x & 31); b < cd.pV0; b += nthreads) {
-            const int64_t i = b + (threadIdx.x & 31);
-            bool viol = false;
-            int32_t x = 0;
-            int nch = 0;
-            if (i < cd.pV0) {
-                x = (int32_t)(B.nU + i);
-                const int c = abc::cnt_load(a, x);
-                viol = c >= prev && c < a.thrV;
-                if (viol) nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
-            }
-            abc::push_add(a, smem[wib].push, pc, viol, x, nch, ls);
+        // the V candidates shrink to degree >= the new bound. The live V vertices of the previous
+        // prefix that miss it (all those past the new prefix among them, their degree being below
+        // it; with a seed chain, also those outside its step-j core) fall first, their rows walked
+        // with decrements that return nothing; the U candidates those decrements took below alpha
+        // are then queued; the cascade does the rest. A fallen U vertex walks only its entries
+        // inside the new prefix (process_items).
+        a.pV = B.pvs[cd.beta_off + j];
+        a.pV_rows = cd.pV0;
+        a.frac_rows = B.fracs[cd.beta_off + j];
+        {
+            unsigned long long e0 = 0, d0 = 0;
+            abc::fall_walk_v(a, smem[wib], pv_prev, prev, a.dead_own != 0, t0, nthreads, ls, e0, d0);
+            ents += e0;
+            sdecs += d0;
         }
-        abc::push_flush(a, smem[wib].push, pc);
+        if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        {
+            unsigned long long sc = 0;
+            abc::fall_scan_u(a, smem[wib], t0, nthreads, ls, sc);
+        }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
@@ -189,6 +201,7 @@ out:
 struct PairRef {
     int32_t chain;  // index into the wave's chains
     int32_t step;
+    int32_t pv;     // V candidate prefix of the pair's beta
 };
 
 // Masks of every pair of a wave, in the caller's ids: one thread per vertex, one byte per pair.
@@ -199,17 +212,17 @@ __global__ void __launch_bounds__(256) k_batch_emit(const int32_t *__restrict__ 
                                                     int32_t npairs, uint8_t *__restrict__ masks_u,
                                                     uint8_t *__restrict__ masks_v) {
     extern __shared__ int32_t sh[];
-    int32_t *pU0 = sh, *pV0 = sh + nchains, *col = sh + 2 * nchains;
-    int32_t *pc = sh + 3 * nchains, *ps = pc + npairs, *pi = ps + npairs;
+    int32_t *pU0 = sh, *col = sh + nchains;
+    int32_t *pc = sh + 2 * nchains, *ps = pc + npairs, *pi = ps + npairs, *pv = pi + npairs;
     for (int i = threadIdx.x; i < nchains; i += blockDim.x) {
         pU0[i] = chains[i].pU0;
-        pV0[i] = chains[i].pV0;
         col[i] = chains[i].col;
     }
     for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
         pc[i] = pairs[i].chain;
         ps[i] = pairs[i].step;
         pi[i] = pidx[i];
+        pv[i] = pairs[i].pv;
     }
     __syncthreads();
     const int64_t n = (int64_t)nU + nV;
@@ -219,7 +232,9 @@ __global__ void __launch_bounds__(256) k_batch_emit(const int32_t *__restrict__ 
         const uint8_t *row = lvl + (size_t)x * lvl_stride;
         for (int p = 0; p < npairs; ++p) {
             const int ch = pc[p];
-            const bool cand = upper ? (x < pU0[ch]) : (x - nU < pV0[ch]);
+            // a candidate of the pair that had not fallen by its step (V vertices that left the
+            // prefix at a later step are never queued: the prefix test places them)
+            const bool cand = upper ? (x < pU0[ch]) : (x - nU < pv[p]);
             const uint8_t v = (cand && __ldg(&row[col[ch]]) > ps[p]) ? 1 : 0;
             if (upper) masks_u[(size_t)pi[p] * nU + i] = v;
             else masks_v[(size_t)pi[p] * nV + (i - nU)] = v;
@@ -248,8 +263,12 @@ struct BatchState {
     int key_chunk = 0;
     // plan
     std::vector<Wave> waves;
-    std::vector<int32_t> betas;
+    std::vector<int32_t> betas, pvs;
+    std::vector<float> fracs;
     int32_t *d_betas = nullptr;
+    int32_t *d_pvs = nullptr;
+    float *d_fracs = nullptr;
+    bool lvl_global = false;            // every chain has its own lvl column (seeding; cleared once per call)
     int nmem = 0;                       // chain workspaces allocated
     std::vector<ChainMem> mem;
     ChainMem *d_mem = nullptr;
@@ -278,6 +297,8 @@ static void destroy_plan(abcore_ctx *ctx, BatchState *b) {
     }
     b->waves.clear();
     ctx->release(b->d_betas);
+    ctx->release(b->d_pvs);
+    ctx->release(b->d_fracs);
     ctx->release(b->prof);
     if (b->ctl_host) cudaFreeHost(b->ctl_host);
     b->ctl_host = nullptr;
@@ -314,11 +335,29 @@ static int batch_grid(abcore_ctx *ctx) {
     return std::max(per_sm, 1) * ctx->num_sms;
 }
 
-// Build the plan for a pair list: chains by alpha, waves, slices, device tables.
+// The removal-step record, n rows of `stride` bytes.
+static int ensure_lvl(abcore_ctx *ctx, BatchState *b, int stride) {
+    if (b->lvl && b->lvl_stride == stride) return ABCORE_OK;
+    ctx->release(b->lvl);
+    b->lvl_stride = stride;
+    return ctx->alloc(&b->lvl, (size_t)std::max<int64_t>(ctx->g.n(), 1) * stride, "batch levels");
+}
+
+constexpr int MAX_LVL_COLS = 64;  // chains with a column of their own in lvl (beyond: one per wave slot)
+
+// Build the plan for a pair list: chains by alpha, waves, seeds, slices, device tables.
+//
+// Chains are sorted by alpha. Without seeding, each wave takes the next chains in that order and
+// chains share lvl columns by their slot in the wave. With seeding (and at most MAX_LVL_COLS
+// chains), every chain has its own column and the chains are dealt to waves round-robin (chain k
+// runs in wave k mod W), so a chain's smaller-alpha neighbours mostly ran in earlier waves: with
+// the same beta steps, the closest such chain's step-j core contains this chain's (the nested
+// property in alpha), and its non-members are queued as known dead.
 static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *alphas, const int32_t *betas) {
     const Graph &g = ctx->g;
     std::map<int32_t, std::vector<int32_t>> by_alpha;
-    for (int32_t i = 0; i < n; ++i) by_alpha[alphas[i]].push_back(betas[i]);
+    for (int32_t i = 0; i < n; ++i)
+        if (alphas[i] >= ctx->prm.batch_plain_below) by_alpha[alphas[i]].push_back(betas[i]);
     struct Chain {
         int32_t alpha;
         std::vector<int32_t> betas;
@@ -335,60 +374,95 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
     const int grid = batch_grid(ctx);
     int per_wave = std::max(1, std::min({MAX_CHAINS_PER_WAVE, grid, b->nmem}));
     if (ctx->prm.batch_wave > 0) per_wave = std::min(per_wave, ctx->prm.batch_wave);
+    const int NW = (C + per_wave - 1) / per_wave;
+    const bool own_cols = ctx->prm.batch_seed && C <= MAX_LVL_COLS;
+    b->lvl_global = own_cols;
+    const int stride = ((own_cols ? C : per_wave) + 3) / 4 * 4;
+    ABC_TRY(ensure_lvl(ctx, b, stride));
     b->betas.clear();
-    b->waves.clear();
-    for (int w0 = 0; w0 < C; w0 += per_wave) {
-        Wave wave;
-        const int cw = std::min(per_wave, C - w0);
+    b->pvs.clear();
+    b->fracs.clear();
+    b->waves.assign(NW, Wave{});
+    std::vector<int> wave_of(C), slot_of(C), col_of(C);
+    for (int k = 0; k < C; ++k) {
+        wave_of[k] = own_cols ? k % NW : k / per_wave;
+        slot_of[k] = own_cols ? k / NW : k % per_wave;
+        col_of[k] = own_cols ? k : slot_of[k];
+    }
+    int seeded = 0;
+    for (int k = 0; k < C; ++k) {
+        const Chain &ch = chains[k];
+        Wave &wave = b->waves[wave_of[k]];
+        ChainDev d{};
+        d.alpha = ch.alpha;
+        d.nsteps = (int32_t)ch.betas.size();
+        d.beta_off = (int32_t)b->betas.size();
+        b->betas.insert(b->betas.end(), ch.betas.begin(), ch.betas.end());
+        const int32_t beta0 = ch.betas[0];
+        for (size_t j = 0; j < ch.betas.size(); ++j) {
+            const int32_t bj = ch.betas[j];
+            b->pvs.push_back((int32_t)cnt_ge(g.cntV_ge, bj));
+            // where the search for a fallen U row's end inside the new prefix starts: the share of
+            // the step-0 prefix's entries that lie below the new bound
+            const double eb = (double)std::max<int64_t>(cnt_ge(g.edgesV_ge, ch.betas[0]), 1);
+            b->fracs.push_back((float)((double)cnt_ge(g.edgesV_ge, bj) / eb));
+        }
+        d.pU0 = (int32_t)cnt_ge(g.cntU_ge, ch.alpha);
+        d.pV0 = (int32_t)cnt_ge(g.cntV_ge, beta0);
+        const int mode = pick_mode(ctx, ch.alpha, beta0, d.pU0, d.pV0);
+        // U counts by row search: a U vertex's plen is then its row's end inside the step-0 V
+        // prefix, where the search for its end inside a later step's prefix ends
+        d.searchU = 1;
+        d.searchV = (mode >> 1) & 1;
+        d.hubcutU = 0;
+        d.hubcutV = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), d.pV0) : 0;
+        if (!d.searchV && d.pV0 > 0) {
+            d.sb = cnt_ge(g.edgesU_ge, ch.alpha);
+            d.eb = g.m;
+        }
+        d.col = col_of[k];
+        d.seed_col = -1;
+        if (own_cols && ctx->prm.batch_seed) {
+            for (int s2 = k - 1; s2 >= 0; --s2)
+                if (wave_of[s2] < wave_of[k] && chains[s2].alpha < ch.alpha && chains[s2].betas == ch.betas) {
+                    d.seed_col = col_of[s2];
+                    seeded++;
+                    break;
+                }
+        }
+        wave.chains.push_back(d);
+    }
+    for (auto &wave : b->waves) {
+        const int cw = (int)wave.chains.size();
         wave.grid = grid;
         int first = 0;
         for (int k = 0; k < cw; ++k) {
-            const Chain &ch = chains[w0 + k];
-            ChainDev d{};
-            d.alpha = ch.alpha;
-            d.nsteps = (int32_t)ch.betas.size();
-            d.beta_off = (int32_t)b->betas.size();
-            b->betas.insert(b->betas.end(), ch.betas.begin(), ch.betas.end());
-            const int32_t beta0 = ch.betas[0];
-            d.pU0 = (int32_t)cnt_ge(g.cntU_ge, ch.alpha);
-            d.pV0 = (int32_t)cnt_ge(g.cntV_ge, beta0);
-            const int mode = pick_mode(ctx, ch.alpha, beta0, d.pU0, d.pV0);
-            d.searchU = mode & 1;
-            d.searchV = (mode >> 1) & 1;
-            d.hubcutU = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntU_ge, ctx->prm.hub_degree), d.pU0) : 0;
-            d.hubcutV = ctx->prm.hub_degree > 0 ? (int32_t)std::min<int64_t>(cnt_ge(g.cntV_ge, ctx->prm.hub_degree), d.pV0) : 0;
-            if (!d.searchU && d.pU0 > 0) {
-                d.sa = g.m + cnt_ge(g.edgesV_ge, beta0);
-                d.ea = 2 * g.m;
-            }
-            if (!d.searchV && d.pV0 > 0) {
-                d.sb = cnt_ge(g.edgesU_ge, ch.alpha);
-                d.eb = g.m;
-            }
+            ChainDev &d = wave.chains[k];
             d.nblocks = grid / cw + (k < grid % cw ? 1 : 0);
             d.first_block = first;
             first += d.nblocks;
-            d.col = k;
-            wave.chains.push_back(d);
         }
-        b->waves.push_back(std::move(wave));
     }
-    // pair -> (wave, chain in wave, step)
+    // pair -> (wave, chain in wave, step); pairs left to single peels have no chain
     for (int32_t i = 0; i < n; ++i) {
+        if (alphas[i] < ctx->prm.batch_plain_below) continue;
         int ci = 0;
         for (; ci < C; ++ci) {
             if (chains[ci].alpha != alphas[i]) continue;
             const auto &bs = chains[ci].betas;
             if (std::binary_search(bs.begin(), bs.end(), betas[i])) break;
         }
-        const int wv = ci / per_wave, k = ci % per_wave;
         const auto &bs = chains[ci].betas;
         const int step = (int)(std::lower_bound(bs.begin(), bs.end(), betas[i]) - bs.begin());
-        b->waves[wv].pairs.push_back({k, step});
-        b->waves[wv].pidx.push_back(i);
+        b->waves[wave_of[ci]].pairs.push_back({slot_of[ci], step, (int32_t)cnt_ge(g.cntV_ge, betas[i])});
+        b->waves[wave_of[ci]].pidx.push_back(i);
     }
     ABC_TRY(ctx->alloc(&b->d_betas, b->betas.size(), "batch betas"));
     ABC_CU(cudaMemcpy(b->d_betas, b->betas.data(), sizeof(int32_t) * b->betas.size(), cudaMemcpyHostToDevice));
+    ABC_TRY(ctx->alloc(&b->d_pvs, b->pvs.size(), "batch prefixes"));
+    ABC_CU(cudaMemcpy(b->d_pvs, b->pvs.data(), sizeof(int32_t) * b->pvs.size(), cudaMemcpyHostToDevice));
+    ABC_TRY(ctx->alloc(&b->d_fracs, b->fracs.size(), "batch prefix shares"));
+    ABC_CU(cudaMemcpy(b->d_fracs, b->fracs.data(), sizeof(float) * b->fracs.size(), cudaMemcpyHostToDevice));
     for (auto &w : b->waves) {
         ABC_TRY(ctx->alloc(&w.d_chains, w.chains.size(), "batch chains"));
         ABC_TRY(ctx->alloc(&w.d_pairs, std::max<size_t>(w.pairs.size(), 1), "batch pairs"));
@@ -402,8 +476,8 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
     ABC_CU(cudaMallocHost(&b->ctl_host, sizeof(PeelCtl) * MAX_CHAINS_PER_WAVE * b->waves.size()));
     if (ctx->prm.log_level >= 2)
         ABC_TRY(ctx->alloc(&b->prof, b->waves.size() * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2), "batch timeline"));
-    ctx->log(1, "batch plan: %d pairs, %d chains in %d waves of up to %d, grid %d blocks", n, C, (int)b->waves.size(),
-             per_wave, grid);
+    ctx->log(1, "batch plan: %d pairs, %d chains in %d waves of up to %d, grid %d blocks, %d seeded chains", n, C,
+             (int)b->waves.size(), per_wave, grid, seeded);
     return ABCORE_OK;
 }
 
@@ -429,7 +503,6 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     }
     b->mem.clear();
     ctx->release(b->d_mem);
-    ctx->release(b->lvl);
     b->nmem = 0;
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
@@ -450,8 +523,6 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     }
     ABC_TRY(ctx->alloc(&b->d_mem, chains, "batch chain table"));
     ABC_CU(cudaMemcpy(b->d_mem, b->mem.data(), sizeof(ChainMem) * chains, cudaMemcpyHostToDevice));
-    b->lvl_stride = ((std::min(chains, MAX_CHAINS_PER_WAVE) + 3) / 4) * 4;
-    ABC_TRY(ctx->alloc(&b->lvl, (size_t)std::max<int64_t>(n, 1) * b->lvl_stride, "batch levels"));
     if (!b->flags) ABC_TRY(ctx->alloc(&b->flags, (size_t)grid * 32, "batch close flags"));
     b->nmem = chains;
     ABC_CU(cudaStreamSynchronize(ctx->stream));
@@ -462,6 +533,7 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
 static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t *d_mv) {
     const Graph &g = ctx->g;
     const int64_t n = g.n();
+    if (b->lvl_global) ABC_CU(cudaMemsetAsync(b->lvl, 0xff, (size_t)n * b->lvl_stride, ctx->stream));
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         Wave &w = b->waves[wi];
         const int cw = (int)w.chains.size();
@@ -469,7 +541,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
             ABC_CU(cudaMemsetAsync(b->mem[c].ctl, 0, sizeof(PeelCtl), ctx->stream));
             ABC_CU(cudaMemsetAsync(b->mem[c].bar, 0, 64 * sizeof(unsigned), ctx->stream));
         }
-        ABC_CU(cudaMemsetAsync(b->lvl, 0xff, (size_t)n * b->lvl_stride, ctx->stream));
+        if (!b->lvl_global) ABC_CU(cudaMemsetAsync(b->lvl, 0xff, (size_t)n * b->lvl_stride, ctx->stream));
         ABC_CU(cudaMemsetAsync(b->flags, 0, sizeof(uint32_t) * (size_t)w.grid * 32, ctx->stream));
         BatchArgs B{};
         B.off = g.off;
@@ -479,6 +551,8 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.chains = w.d_chains;
         B.mem = b->d_mem;
         B.betas = b->d_betas;
+        B.pvs = b->d_pvs;
+        B.fracs = b->d_fracs;
         B.nchains = cw;
         B.lvl = b->lvl;
         B.lvl_stride = b->lvl_stride;
@@ -504,7 +578,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         ctx->stats.launches++;
         if (!w.pairs.empty()) {
             const int np = (int)w.pairs.size();
-            const size_t shm = sizeof(int32_t) * (3 * cw + 3 * np);
+            const size_t shm = sizeof(int32_t) * (2 * cw + 4 * np);
             if (shm > 200 * 1024) return ctx->fail(ABCORE_EINVAL, "too many pairs in one batch wave");
             if (shm > 48 * 1024)
                 ABC_CU(cudaFuncSetAttribute(k_batch_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -532,11 +606,16 @@ int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32
     if (!same || !b->use_graph) {
         destroy_plan(ctx, b);
         std::map<int32_t, int> na;
-        for (int32_t i = 0; i < n; ++i) na[alphas[i]]++;
+        for (int32_t i = 0; i < n; ++i)
+            if (alphas[i] >= ctx->prm.batch_plain_below) na[alphas[i]]++;
         int want = std::min<int>((int)na.size(), MAX_CHAINS_PER_WAVE);
         if (ctx->prm.batch_wave > 0) want = std::min(want, ctx->prm.batch_wave);
-        ABC_TRY(ensure_memory(ctx, b, want));
-        ABC_TRY(make_plan(ctx, b, n, alphas, betas));
+        if (want > 0) {
+            ABC_TRY(ensure_memory(ctx, b, want));
+            ABC_TRY(make_plan(ctx, b, n, alphas, betas));
+        } else {
+            b->waves.clear();
+        }
         b->key_a.assign(alphas, alphas + n);
         b->key_b.assign(betas, betas + n);
         b->key_mu = d_masks_u;
@@ -585,10 +664,26 @@ int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32
     } else {
         ABC_TRY(enqueue_batch(ctx, b, d_masks_u, d_masks_v));
     }
+    // pairs of small alpha are peeled one at a time by the single peel, always the plain one (the
+    // batch stays index-free): there a chain would walk far more rows than the separate peels,
+    // whose degree prefixes leave most of them out
+    int plain_rc = ABCORE_OK;
+    bool plain_any = false;
+    for (int32_t i = 0; i < n && !plain_rc; ++i) {
+        if (alphas[i] >= ctx->prm.batch_plain_below) continue;
+        plain_any = true;
+        plain_rc = peel_compute(ctx, alphas[i], betas[i], d_masks_u + (size_t)i * g.nU, d_masks_v + (size_t)i * g.nV,
+                                false, false);
+    }
     if (timed) ABC_CU(cudaEventRecord(b->ev1, ctx->stream));
     ABC_CU(cudaGetLastError());
     (void)sync_and_check;
     ABC_CU(cudaStreamSynchronize(ctx->stream));
+    if (plain_any) {
+        const int frc = peel_finish(ctx);
+        if (!plain_rc) plain_rc = frc;
+    }
+    if (plain_rc) return plain_rc;
     int first_err = 0;
     abcore_stats &s = ctx->stats;
     for (size_t wi = 0; wi < b->waves.size(); ++wi)

@@ -60,6 +60,11 @@ struct PeelArgs {
     int32_t cU, cV;          // vertices below these (U [0,cU), V [nU, nU+cV)) are certain members:
                              // never counted, decremented or removed (0 for the plain peel)
     int32_t thrU, thrV;      // alpha, beta
+    // U rows' plen counts neighbours below nU + pV_rows; when a batch chain's step has narrowed
+    // the V prefix (pV < pV_rows), a fallen U vertex walks only its row's entries below nU + pV,
+    // found by a row search that starts from the share frac_rows (0: never narrowed)
+    int32_t pV_rows;
+    float frac_rows;
     int32_t chunk;           // adjacency entries per work item
     int32_t batch_entries;   // entries one warp walks per batch at most (the rest is re-queued)
     int32_t flush_steps;     // steps a pending push may wait before its warp flushes
@@ -79,6 +84,11 @@ struct PeelArgs {
     // lvl[vertex * lvl_stride + lvl_col] (lvl == nullptr: no record)
     uint8_t *lvl;
     int32_t lvl_stride, lvl_col, step;
+    // seeding of a batch chain (seed_col >= 0): a candidate outside the same step's core of the
+    // chain whose lvl column that is (its lvl <= step) is known dead and queued whatever its
+    // count; dead_own then makes a crossing check the vertex's own lvl column first, so a vertex
+    // queued that way is never queued twice
+    int32_t dead_own, seed_col;
     int32_t *corev;          // if set, a vertex queued during `step` gets corev[vertex] = step
     // round0: the count init lists its violators in l0 (not the queue); k_round0 walks their rows
     // with atomics that return nothing, and the scan then queues every other candidate below its
@@ -122,6 +132,12 @@ struct Params {
     int emit_bitmap_min_pct = 0;   // gather: test removal in the caller-order bitmap when |P| >= this
                                    // % of n (each removal then sets its bit), else read the count
     double probe_bytes = 32.0;     // cost model: bytes charged per search probe
+    int batch_plain_below = 0; // abcore_compute_batch: pairs with alpha below this are peeled one by one
+                               // with the single (plain) peel instead of in chains; the autotuner
+                               // picks it (small alphas leave chains with huge U candidate sets)
+    int batch_seed = 0;        // 1: a batch chain is seeded from the finished chain of the next
+                               // smaller alpha with the same betas (its non-members are queued at
+                               // once); measured no faster on the power-law grids, so off by default
     int batch_wave = 4;        // chains sharing the GPU at once (0 = as many as fit, up to 32);
                                // 4 measured best on a 500M-edge graph (counts stay closer to L2)
     int debug_stall_slots = 0; // test hook: queue slots reserved but never written

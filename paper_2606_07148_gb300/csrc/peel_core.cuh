@@ -133,6 +133,19 @@ __device__ __forceinline__ void mark_fallen(const PeelArgs &a, int32_t x, int32_
     atomicOr(&a.fallen[u >> 5], 1u << (u & 31));
 }
 
+// Whether vertex x has not fallen in this chain yet (always true outside batch chains).
+__device__ __forceinline__ bool chain_alive(const PeelArgs &a, int32_t x) {
+    return a.lvl == nullptr || __ldcg(&a.lvl[(size_t)x * a.lvl_stride + a.lvl_col]) == 0xFF;
+}
+
+// Whether candidate x is known to be outside this step's core before any count is looked at.
+__device__ __forceinline__ bool known_dead(const PeelArgs &a, int32_t x) {
+    if (a.lvl == nullptr) return false;
+    const uint8_t *row = a.lvl + (size_t)x * a.lvl_stride;
+    return (a.dead_own && __ldcg(&row[a.lvl_col]) != 0xFF) ||
+           (a.seed_col >= 0 && __ldcg(&row[a.seed_col]) <= (uint8_t)a.step);
+}
+
 template <int CAP>
 __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, int &pc, bool want, int32_t y, int nch,
                                          LaneStats &ls, bool fallen = true, int c0 = 0) {
@@ -140,7 +153,11 @@ __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, in
         ls.pushes++;
         // a removal with an empty row is never queued, so nothing else would record it
         if (nch == 0 && a.fallen != nullptr) mark_fallen(a, y, __ldg(&a.new2old[y]));
-        if (a.lvl) a.lvl[(size_t)y * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+        if (a.lvl) {
+            // the step a vertex first falls at
+            uint8_t *l = a.lvl + (size_t)y * a.lvl_stride + a.lvl_col;
+            if (*l == 0xFF) *l = (uint8_t)a.step;
+        }
         if (a.corev) a.corev[y] = a.step;
     }
     if (a.removed) {
@@ -162,6 +179,53 @@ __device__ __forceinline__ void push_add(const PeelArgs &a, PushBuf<CAP> &pb, in
 
 __device__ __forceinline__ int chunks_of(int len, int chunk) { return (len + chunk - 1) / chunk; }
 
+
+// Length of the prefix of the sorted row adj[s, e) (s < e) holding ids below `bound`: the row's
+// candidate neighbours. The search reads whole 32-byte sectors (the 8 entries of the aligned
+// sector, clipped to the open range) and starts at s + frac * (e - s), frac being the share of
+// the whole layer's adjacency entries that lie below the bound -- where the boundary of a row
+// whose neighbours are drawn like everyone else's falls. From there it gallops outward in
+// doubling steps until the boundary is bracketed, then bisects. The result does not depend on
+// frac; a good guess settles most rows in one sector where bisection reads log2(length / 8).
+// `probes` counts the sectors read.
+__device__ __forceinline__ int row_prefix(const int32_t *__restrict__ adj, int64_t s, int64_t e, int32_t bound,
+                                          float frac, unsigned long long &probes) {
+    const int32_t *row = adj + s;
+    const int d = (int)(e - s);
+    int lo = 0, hi = d;  // the boundary (first index holding an id >= bound, or d) is in [lo, hi]
+    int p = (int)(frac * (float)d);
+    p = p < 0 ? 0 : (p >= d ? d - 1 : p);
+    const int mis = (int)((reinterpret_cast<uintptr_t>(row) >> 2) & 7);  // entries past a sector start
+    int dist = 8;
+    int dir = 0;  // 0: first probe; +1 / -1: galloping right / left; 2: bracketed, bisecting
+    while (lo < hi) {  // p is in [lo, hi): every pass shrinks the range
+        const int w = ((p + mis) & ~7) - mis;
+        const int w0 = max(w, lo), w1 = min(w + 8, hi);
+        int below = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = w + k;
+            if (i >= w0 && i < w1) below += __ldg(&row[i]) < bound ? 1 : 0;
+        }
+        probes++;
+        if (below > 0 && below < w1 - w0) return w0 + below;
+        const int want = below == 0 ? -1 : 1;
+        if (below == 0) hi = w0;
+        else lo = w1;
+        if (lo >= hi) break;
+        if (dir == 0 || dir == want) {
+            dir = want;
+            // (a row is shorter than 2^31, so w1 - 1 + dist stays in range: dist < 2 * d)
+            p = want > 0 ? w1 - 1 + dist : w0 - dist;
+            dist <<= 1;
+            p = p < lo ? lo : (p >= hi ? hi - 1 : p);
+        } else {
+            dir = 2;
+        }
+        if (dir == 2) p = lo + ((hi - lo) >> 1);
+    }
+    return lo;
+}
 
 // Entries handled per lane per step by the streaming and cascade loops: the loads, then the
 // atomics, of one step are independent, so they overlap instead of waiting one at a time.
@@ -191,8 +255,17 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
         x = (int32_t)(it >> 32);
         c = (int)(it & 0xffffffffu);
         if (a.fallen != nullptr && c == 0) o = __ldg(&a.new2old[x]);  // caller id, for the bitmap
-        const int rl = row_len_of(a, x);
-        start = __ldg(&a.off[x]) + (long long)c * a.chunk;
+        int rl = row_len_of(a, x);
+        const long long s0 = __ldg(&a.off[x]);
+        // a chain step with a narrower V prefix: a U row's candidates are its entries below it
+        if (x < a.nU && a.pV < a.pV_rows && rl > 0) {
+            unsigned long long probes = 0;
+            rl = row_prefix(a.adj, s0, s0 + rl, a.nU + a.pV, a.frac_rows, probes);
+        }
+        // a count of 0 means every candidate neighbour has fallen and decremented this vertex
+        // already: walking its row would only decrement fallen vertices, so the walk is skipped
+        if (rl > 0 && cnt_load(a, x) == 0) rl = 0;
+        start = s0 + (long long)c * a.chunk;
         len = min(a.chunk, rl - c * a.chunk);
         if (len < 0) len = 0;
         if (c == 0 && rl > a.chunk) more = chunks_of(rl, a.chunk) - 1;
@@ -247,8 +320,9 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (hit[u]) ls.decs++;
-            // the crossing decrement: y had a count of 1 or more, so its row is not empty
-            push_add(a, sm.push, pc, hit[u] && old[u] == thr[u], y[u], 1, ls);
+            // the crossing decrement: y had a count of 1 or more, so its row is not empty (a vertex a
+            // seeded chain step queued as known dead may still cross: it is not queued twice)
+            push_add(a, sm.push, pc, hit[u] && old[u] == thr[u] && (a.dead_own == 0 || chain_alive(a, y[u])), y[u], 1, ls);
         }
         ++since;
         if (pc >= 32 || (pc > 0 && since >= a.flush_steps)) {
@@ -460,11 +534,13 @@ __device__ __forceinline__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl
             atomicExch(bar, 0u);
             if (watch) bar[16] = ld_relaxed(watch) >= limit ? 1u : 0u;
             if (fixup) {
-                // the cascade closed the queue: the tickets it voided, [tail, old head), were
-                // emptied by their holders, so the next step's tickets restart at tail
-                const unsigned long long t = ld_relaxed(&ctl->tail);
-                atomicExch(&ctl->head, t);
-                atomicExch(&ctl->done, t);
+                // the cascade closed the queue: every reserved slot [0, tail) was processed and
+                // emptied by its consumer, and the tickets it voided, [tail, old head), were never
+                // filled; so the whole queue is empty and the next step starts at slot 0 (a step
+                // never needs more room than one peel, however many steps the chain has)
+                atomicExch(&ctl->tail, 0ull);
+                atomicExch(&ctl->head, 0ull);
+                atomicExch(&ctl->done, 0ull);
             }
             __threadfence();
             atomicAdd(bar + 32, 1u);
@@ -486,53 +562,6 @@ __device__ __forceinline__ bool group_barrier(unsigned *bar, int G, PeelCtl *ctl
     }
     __syncthreads();
     return ok != 0;
-}
-
-// Length of the prefix of the sorted row adj[s, e) (s < e) holding ids below `bound`: the row's
-// candidate neighbours. The search reads whole 32-byte sectors (the 8 entries of the aligned
-// sector, clipped to the open range) and starts at s + frac * (e - s), frac being the share of
-// the whole layer's adjacency entries that lie below the bound -- where the boundary of a row
-// whose neighbours are drawn like everyone else's falls. From there it gallops outward in
-// doubling steps until the boundary is bracketed, then bisects. The result does not depend on
-// frac; a good guess settles most rows in one sector where bisection reads log2(length / 8).
-// `probes` counts the sectors read.
-__device__ __forceinline__ int row_prefix(const int32_t *__restrict__ adj, int64_t s, int64_t e, int32_t bound,
-                                          float frac, unsigned long long &probes) {
-    const int32_t *row = adj + s;
-    const int d = (int)(e - s);
-    int lo = 0, hi = d;  // the boundary (first index holding an id >= bound, or d) is in [lo, hi]
-    int p = (int)(frac * (float)d);
-    p = p < 0 ? 0 : (p >= d ? d - 1 : p);
-    const int mis = (int)((reinterpret_cast<uintptr_t>(row) >> 2) & 7);  // entries past a sector start
-    int dist = 8;
-    int dir = 0;  // 0: first probe; +1 / -1: galloping right / left; 2: bracketed, bisecting
-    while (lo < hi) {  // p is in [lo, hi): every pass shrinks the range
-        const int w = ((p + mis) & ~7) - mis;
-        const int w0 = max(w, lo), w1 = min(w + 8, hi);
-        int below = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = w + k;
-            if (i >= w0 && i < w1) below += __ldg(&row[i]) < bound ? 1 : 0;
-        }
-        probes++;
-        if (below > 0 && below < w1 - w0) return w0 + below;
-        const int want = below == 0 ? -1 : 1;
-        if (below == 0) hi = w0;
-        else lo = w1;
-        if (lo >= hi) break;
-        if (dir == 0 || dir == want) {
-            dir = want;
-            // (a row is shorter than 2^31, so w1 - 1 + dist stays in range: dist < 2 * d)
-            p = want > 0 ? w1 - 1 + dist : w0 - dist;
-            dist <<= 1;
-            p = p < lo ? lo : (p >= hi ? hi - 1 : p);
-        } else {
-            dir = 2;
-        }
-        if (dir == 2) p = lo + ((hi - lo) >> 1);
-    }
-    return lo;
 }
 
 // Candidate counts (the scan phase): thread t of nthreads handles candidates t, t + nthreads, ...
@@ -583,7 +612,7 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                 cnt_store(a, x[k], len);
                 a.plen[x[k]] = len;
                 inits++;
-                viol = len < (upper ? a.thrU : a.thrV);
+                viol = len < (upper ? a.thrU : a.thrV) || known_dead(a, x[k]);
                 nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
             }
             if (a.round0) {
@@ -701,7 +730,8 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
             int nch = 0;
             if (x[k] >= 0) {
                 const int thr = x[k] < a.nU ? a.thrU : a.thrV;
-                viol = c[k] < thr;
+                // (a candidate the count init queued as known dead is not queued twice)
+                viol = c[k] < thr && !(a.dead_own && !chain_alive(a, x[k]));
                 if (viol) {
                     const int pl = __ldcg(&a.plen[x[k]]);
                     if (a.round0 && pl < thr) viol = false;  // an initial violator: round0 walked it
@@ -713,6 +743,93 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
         }
     }
     push_flush(a, pb, pc);
+}
+
+// A batch chain's step with a higher V bound (thrV, prefix a.pV), run before its cascade: every
+// live V candidate of the previous prefix [nU, nU + pv_prev) whose count misses the new bound --
+// all those past the new prefix among them, their degree being below it -- falls now. Its fall is
+// recorded (lvl) and its row is walked at once by the warp, lanes sharing out the 32 vertices'
+// entries evenly, with decrements that return nothing: no crossing is looked for here, the U scan
+// after it (fall_scan_u) finds every U candidate these decrements took below alpha. A vertex whose
+// count is 0 has no live neighbour left and walks nothing. With `by_lvl` a V vertex is live iff
+// its lvl is unset (seeded chains queue known-dead vertices whatever their count); otherwise iff
+// its count meets the previous bound prev_thrV. Warp-collective; `t0` is warp-aligned.
+__device__ __forceinline__ void fall_walk_v(const PeelArgs &a, WarpSmem &sm, int32_t pv_prev, int32_t prev_thrV,
+                                            bool by_lvl, int64_t t0, int64_t nthreads, LaneStats &ls,
+                                            unsigned long long &ents, unsigned long long &decs) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = t0 - lane; b < pv_prev; b += nthreads) {
+        const int64_t i = b + lane;
+        const int32_t x = (int32_t)(a.nU + (i < pv_prev ? i : 0));
+        bool fall = false;
+        int len = 0;
+        long long s = 0;
+        if (i < pv_prev) {
+            const int c = cnt_load(a, x);
+            const bool live = by_lvl ? chain_alive(a, x) : c >= prev_thrV;
+            fall = live && (c < a.thrV || (a.seed_col >= 0 && known_dead(a, x)));
+            if (fall) {
+                a.lvl[(size_t)x * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+                ls.pushes++;
+                if (c > 0) {
+                    len = __ldcg(&a.plen[x]);
+                    s = __ldg(&a.off[x]);
+                }
+            }
+        }
+        const int incl = warp_incl_scan(len);
+        const int L = __shfl_sync(ABC_FULL, incl, 31);
+        if (L == 0) continue;
+        sm.start[lane] = s;
+        sm.excl[lane] = incl - len;
+        __syncwarp();
+        int j = 0;
+        for (int e0 = 0; e0 < L; e0 += 32 * ILP) {
+            int32_t y[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int e = e0 + 32 * u + lane;
+                y[u] = -1;
+                if (e < L) {
+                    while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
+                    y[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                if (y[u] < 0) continue;
+                ents++;
+                if (y[u] < a.pU && y[u] >= a.cU) {  // a U candidate
+                    cnt_dec_noret(a, y[u]);
+                    decs++;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// After fall_walk_v: every U candidate that was live (lvl unset) and whose count is now below
+// alpha falls, queued for the cascade. Warp-collective; `t0` is warp-aligned.
+__device__ __forceinline__ void fall_scan_u(const PeelArgs &a, WarpSmem &sm, int64_t t0, int64_t nthreads,
+                                            LaneStats &ls, unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    int pc = 0;
+    for (int64_t b = t0 - lane; b < a.pU; b += nthreads) {
+        const int64_t i = b + lane;
+        const int32_t x = (int32_t)(i < a.pU ? i : 0);
+        bool fall = false;
+        int nch = 0;
+        if (i < a.pU && i >= a.cU) {
+            scanned++;
+            if (cnt_load(a, x) < a.thrU && chain_alive(a, x)) {
+                fall = true;
+                nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
+            }
+        }
+        push_add(a, sm.push, pc, fall, x, nch, ls);
+    }
+    push_flush(a, sm.push, pc);
 }
 
 __device__ __forceinline__ void flush_stats(const PeelArgs &a, LaneStats &ls) {

@@ -6,7 +6,8 @@
 // count is found by search rather than by the violator stream (the hub threshold), how a layer's
 // counts are taken at all (the stream/search switch, weighted by the cost of one search probe),
 // and when survivors are scattered into zeroed masks rather than gathered. The batch adds how
-// many chains share the GPU at once. The tuner runs coordinate descent over these, timing each
+// many chains share the GPU at once, below which alpha pairs are left to single peels, and
+// whether chains are seeded from smaller-alpha chains. The tuner runs coordinate descent over these, timing each
 // setting with CUDA events on the context's stream on a sample of (alpha, beta) queries, with the
 // L2 flushed (a 256 MB write) before every timed run, and leaves the fastest setting on the
 // context. Every setting computes the same cores: only time changes.
@@ -71,6 +72,8 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
     const bool batch = (what & ABCORE_TUNE_BATCH) != 0;
     std::vector<Knob> knobs;
     if (batch) {
+        knobs.push_back({"batch_plain_below", {0, 2, 4, 8, 16, 32, 64, 128}});
+        knobs.push_back({"batch_seed", {0, 1}});
         knobs.push_back({"batch_wave", {2, 4, 8, 16}});
         knobs.push_back({"blocks_per_sm", {0, 3}});
         knobs.push_back({"chunk", {512, 1024, 2048}});

@@ -24,6 +24,11 @@ WORKLOADS = {
     "billion-100Mx50M-1500M": dict(nU=100_000_000, nV=50_000_000, m=1_500_000_000, gamma_u=2.0,
                                    gamma_v=2.3, seed=3, kmax=None,
                                    pairs=[(64, 64)] + grid_pairs(8, 1, 1024)),
+    # the billion-scale recipe at a fifth of the vertices and a fifth of the edges (2.6 GB of
+    # CSR): small enough for a profiler that replays each launch many times, with the counts of
+    # a (64, 64) query still far beyond the L2
+    "profile-20Mx10M-300M": dict(nU=20_000_000, nV=10_000_000, m=300_000_000, gamma_u=2.0,
+                                 gamma_v=2.3, seed=3, kmax=None, pairs=[(64, 64)]),
     # serving: seed 4, 10M x 5M, 200M edges, exponents 2.1 / 2.2, 100k updates
     "serve-10Mx5M-200M": dict(nU=10_000_000, nV=5_000_000, m=200_000_000, gamma_u=2.1,
                               gamma_v=2.2, seed=4, kmax=None, n_ops=100_000,

@@ -126,3 +126,60 @@ def test_batch_with_32_bit_counts(small):
     mu32, mv32 = _check_batch(core, nU, nV, off, adj, pairs)
     assert np.array_equal(mu16, mu32) and np.array_equal(mv16, mv32)
     core.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("wave", [1, 3])
+def test_batch_seeding_and_waves(small, seed, wave):
+    # with and without seeding from the finished chain of a smaller alpha; one chain per wave
+    # (every chain but the first seeded) and three (chains of the first wave unseeded)
+    nU, nV, eu, ev, off, adj = small
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.set_param("batch_seed", seed)
+    core.set_param("batch_wave", wave)
+    pairs = synth.grid_pairs(8, 1, 64)
+    _check_batch(core, nU, nV, off, adj, pairs)
+    # the same list twice: the replay starts from a cleared record
+    _check_batch(core, nU, nV, off, adj, pairs)
+    core.close()
+
+
+def test_batch_more_chains_than_own_record_columns(small):
+    # beyond 64 distinct alphas the chains share record columns by wave slot (no seeding)
+    nU, nV, eu, ev, off, adj = small
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.set_param("batch_seed", 1)
+    pairs = [(a, b) for a in range(1, 71) for b in (1, 3, 9)]
+    _check_batch(core, nU, nV, off, adj, pairs)
+    core.close()
+
+
+def test_batch_deep_beta_ladders_mid_size_power_law():
+    # deep beta ladders on a skewed graph: every step moves U rows' boundaries across many V ids
+    nU, nV, m = 400_000, 200_000, 8_000_000
+    eu, ev = synth.chung_lu_edges(nU, nV, m, 2.0, 2.3, seed=14, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, eu.cpu().numpy(), ev.cpu().numpy())
+    pairs = synth.grid_pairs(8, 1, 1024) + [(2, b) for b in range(2, 60, 3)]
+    for seed in (0, 1):
+        core.set_param("batch_seed", seed)
+        _check_batch(core, nU, nV, off, adj, pairs)
+    core.close()
+
+
+@pytest.mark.parametrize("below", [0, 4, 1 << 30])
+def test_batch_small_alphas_left_to_single_peels(small, below):
+    # pairs with alpha below the split are computed by the single plain peel into their rows, the
+    # rest by chains; every pair equals the oracle's, whatever the split (all chains, some, none)
+    nU, nV, eu, ev, off, adj = small
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    core.core_numbers()  # prepared core numbers must not leak the pruned peel into the batch
+    core.set_param("batch_plain_below", below)
+    pairs = synth.grid_pairs(8, 1, 64) + [(0, 5), (5, 0)]
+    _check_batch(core, nU, nV, off, adj, pairs)
+    _check_batch(core, nU, nV, off, adj, pairs)
+    core.close()
