@@ -120,6 +120,8 @@ struct Params {
                                // throughput (1.5B edges, (64,64): 2.01 -> 1.74 ms); costs where it is
                                // latency-bound (80M edges, (50,50): 0.30 -> 0.53 ms). The autotuner
                                // decides per workload.
+    int round0_variant = 0;    // k_round0's compiled (entries per lane per step, blocks per SM) pair:
+                               // 0 (8, any), 1 (4, 8), 2 (16, 4), 3 (8, 8); 4: rows four at a time
     int pdl = 1;               // single peel: launch the kernels after the count init as
                                // programmatic dependents of the one before (each waits for its
                                // predecessor on the device; the launch latency overlaps its tail)

@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
 // for here, k_scan finds every candidate the round took below its bound. Lane l of a warp takes
 // list entry base + l and the warp balances their rows' entries over its lanes; the next group's
 // entries are loaded while this group's rows are walked.
-// (Its entries per lane per step, R0_ILP, are twice the cascade's: nothing waits on the atomics,
-// so only the adjacency loads' latency has to be covered.)
-constexpr int R0_ILP = 8;
-
-__global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
+// Entries per lane per step (R0_ILP) and the blocks an SM must hold (R0_MINB, which caps the
+// registers) are compiled in a few combinations (k_round0_variant picks one; the autotuner
+// decides): nothing waits on the atomics, so only the adjacency loads' latency has to be covered,
+// by entries in flight per lane or by warps per SM.
+template <int R0_ILP, int R0_MINB>
+__global__ void __launch_bounds__(256, R0_MINB) k_round0(PeelArgs a) {
     __shared__ long long s_start[256 / 32][32];
     __shared__ int s_excl[256 / 32][32];
     __shared__ int s_upper[256 / 32][32];
@@ -152,6 +153,73 @@ __global__ void __launch_bounds__(256) k_round0(PeelArgs a) {
             }
         }
         __syncwarp();
+    }
+    ents = (unsigned long long)abc::warp_sum64((long long)ents);
+    decs = (unsigned long long)abc::warp_sum64((long long)decs);
+    if (lane == 0) {
+        if (ents) atomicAdd(&a.ctl->st[ST_STREAM], ents);
+        if (decs) atomicAdd(&a.ctl->st[ST_SDECS], decs);
+    }
+}
+
+// The same walk with the rows taken four at a time by the whole warp: lanes read consecutive
+// entries of one row (coalesced), two 32-entry chunks of each of the four rows in flight, so no
+// entry has to look up its row; lanes past a row's end idle (the rows are short, each below its
+// bound). Rows longer than 64 entries finish in a loop.
+__global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
+    const int64_t nl0 = (int64_t)a.ctl->l0n;  // written by k_init, earlier on the stream
+    unsigned long long ents = 0, decs = 0;
+    longlong2 nxt = make_longlong2(0, 0);
+    if (gw * 32 + lane < nl0) nxt = __ldg(&a.l0[gw * 32 + lane]);
+    for (int64_t g0 = gw * 32; g0 < nl0; g0 += nw * 32) {
+        const longlong2 cur = nxt;  // {0, 0} past the end: an empty row
+        const int64_t g1 = g0 + nw * 32 + lane;
+        nxt = g1 < nl0 ? __ldg(&a.l0[g1]) : make_longlong2(0, 0);
+        const int mylen = (int)(cur.y & 0x7fffffff);
+        const int myup = (cur.y & L0_UPPER) != 0;
+        for (int r0 = 0; r0 < 32; r0 += 4) {
+            long long st[4];
+            int len[4], up[4];
+            int32_t y[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                st[k] = __shfl_sync(ABC_FULL, cur.x, r0 + k);
+                len[k] = __shfl_sync(ABC_FULL, mylen, r0 + k);
+                up[k] = __shfl_sync(ABC_FULL, myup, r0 + k);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                y[2 * k] = lane < len[k] ? abc::ld_adj(&a.adj[st[k] + lane]) : -1;
+                y[2 * k + 1] = lane + 32 < len[k] ? abc::ld_adj(&a.adj[st[k] + lane + 32]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (y[u] < 0) continue;
+                ents++;
+                int32_t t;
+                if (abc::cand_of(a, y[u], up[u >> 1] != 0, t) && (t > 0 || !a.skip_zero)) {
+                    abc::cnt_dec_noret(a, y[u]);
+                    decs++;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                for (int e = 64 + lane; e < len[k]; e += 32) {
+                    const int32_t z = abc::ld_adj(&a.adj[st[k] + e]);
+                    ents++;
+                    int32_t t;
+                    if (abc::cand_of(a, z, up[k] != 0, t) && (t > 0 || !a.skip_zero)) {
+                        abc::cnt_dec_noret(a, z);
+                        decs++;
+                    }
+                }
+            }
+        }
     }
     ents = (unsigned long long)abc::warp_sum64((long long)ents);
     decs = (unsigned long long)abc::warp_sum64((long long)decs);
@@ -565,7 +633,13 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             // the initial candidate violators' rows (their count is below the bound, so each row
             // is shorter than the bound)
             const int64_t gr = std::min<int64_t>((Pu + 255) / 256, (int64_t)ctx->num_sms * 16);
-            ABC_CU(launch_k(pdl && prev_k, k_round0, gr, 256, ctx->stream, a));
+            switch (ctx->prm.round0_variant) {
+                case 1: ABC_CU(launch_k(pdl && prev_k, k_round0<4, 8>, gr, 256, ctx->stream, a)); break;
+                case 2: ABC_CU(launch_k(pdl && prev_k, k_round0<16, 4>, gr, 256, ctx->stream, a)); break;
+                case 3: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 8>, gr, 256, ctx->stream, a)); break;
+                case 4: ABC_CU(launch_k(pdl && prev_k, k_round0_rows, gr, 256, ctx->stream, a)); break;
+                default: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 1>, gr, 256, ctx->stream, a)); break;
+            }
             si.has_stream = true;
             ctx->stats.launches++;
         }

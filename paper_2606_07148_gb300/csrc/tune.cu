@@ -88,6 +88,7 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
         knobs.push_back({"emit_scatter_max_pct", {0, 5, 25}});
         knobs.push_back({"emit_bitmap_min_pct", {0, 50, 101}});
         knobs.push_back({"round0", {0, 1}});
+        knobs.push_back({"round0_variant", {0, 2, 4}});
     }
     Timer T;
     uint8_t *mu = nullptr, *mv = nullptr;

@@ -273,18 +273,22 @@ def test_measure_atomics_reports_rates():
 @pytest.mark.parametrize("mode", [1, 2, 3])
 def test_round0_first_round_without_returns(mode):
     # the initial candidate violators' rows walked by k_round0 (no-return decrements, then a scan
-    # for what they took below the bound), in every mode with a searched layer, plain and pruned
+    # for what they took below the bound), in every mode with a searched layer, plain and pruned,
+    # with every compiled walk (rows longer than 64 entries included: bounds up to 150)
     nU, nV, eu, ev = synth.make_graph("peel-2000x1500-20k")
     core = ABCore(0)
     core.load_edges(nU, nV, eu.cuda(), ev.cuda())
     off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
     core.set_param("round0", 1)
     core.set_param("mode", mode)
-    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8)]
-    for a, b in pairs:
-        mu, mv = core.compute(a, b)
-        wu, wv = oracle.peel(nU, nV, off, adj, a, b)
-        assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (mode, a, b)
+    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8), (70, 3), (2, 150)]
+    for variant in range(5):
+        core.set_param("round0_variant", variant)
+        for a, b in pairs:
+            mu, mv = core.compute(a, b)
+            wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (mode, variant, a, b)
+    core.set_param("round0_variant", 0)
     if mode == 3:
         core.core_numbers()
         core.set_param("algo", 2)
@@ -402,10 +406,11 @@ def test_round0_violator_list_longer_than_the_grid():
         if (a, b) == (4, 4):
             assert n_viol > 2 * lanes, (n_viol, lanes)  # several groups per warp
         wu, wv = oracle.peel(nU, nV, off, adj, a, b)
-        for r0 in (0, 1):
+        for r0, variant in ((0, 0), (1, 0), (1, 4)):
             core.set_param("round0", r0)
+            core.set_param("round0_variant", variant)
             mu, mv = core.compute(a, b)
-            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (a, b, r0)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (a, b, r0, variant)
     core.close()
 
 
