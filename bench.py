@@ -800,12 +800,17 @@ def run_serve(args, rank, world, local):
                 got += len(out)
         gc.enable()
         core.serve_stop()
+        sst = core.stats()
         lat_ms = (done_t - sched) * 1e3
         elapsed = done_t.max()
         results[str(rate)] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 4),
                               "p99_ms": round(float(np.percentile(lat_ms, 99)), 4),
                               "max_ms": round(float(lat_ms.max()), 4),
-                              "achieved_ops_per_s": round(n_ops / elapsed, 1)}
+                              "achieved_ops_per_s": round(n_ops / elapsed, 1),
+                              "re_peel": {"regions": sst["serve_regions"],
+                                          "region_vertices_per_region": round(sst["serve_region_vertices"] / max(sst["serve_regions"], 1), 2),
+                                          "cascades": sst["serve_cascades"],
+                                          "vertices_per_cascade": round(sst["serve_cascade_vertices"] / max(sst["serve_cascades"], 1), 2)}}
         answers[rate] = in_core.tolist()
         core.close()
     clk = clocks.stop()

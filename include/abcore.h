@@ -90,6 +90,10 @@ typedef struct {
                                 the first round walked without returns ("round0")              */
     int64_t scope_queries;   /* on-the-fly queries answered with the component scope            */
     int64_t scope_vertices;  /* vertices those queries re-peeled (their components' sizes)      */
+    int64_t serve_regions;   /* served inserts that grew a region to peel (summed over targets) */
+    int64_t serve_region_vertices; /* vertices in those regions                                 */
+    int64_t serve_cascades;  /* served deletes that cascaded inside a target core              */
+    int64_t serve_cascade_vertices; /* vertices those cascades removed                          */
 } abcore_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------------- */

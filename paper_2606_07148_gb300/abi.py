@@ -57,6 +57,8 @@ class abcore_stats(ctypes.Structure):
         ("kernel_ms", ctypes.c_double * K_KINDS), ("mode", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
         ("round0_rows", ctypes.c_int64), ("scope_queries", ctypes.c_int64), ("scope_vertices", ctypes.c_int64),
+        ("serve_regions", ctypes.c_int64), ("serve_region_vertices", ctypes.c_int64),
+        ("serve_cascades", ctypes.c_int64), ("serve_cascade_vertices", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -451,6 +451,12 @@ int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out) {
     *out = ctx->stats;
     out->device_bytes = ctx->dev_bytes;
     out->peak_device_bytes = ctx->peak_bytes;
+    int64_t sv[4];
+    serve_counters(ctx, sv);
+    out->serve_regions = sv[0];
+    out->serve_region_vertices = sv[1];
+    out->serve_cascades = sv[2];
+    out->serve_cascade_vertices = sv[3];
     return ABCORE_OK;
 }
 

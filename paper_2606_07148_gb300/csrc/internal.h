@@ -369,6 +369,9 @@ int serve_materialize(abcore_ctx *ctx);  // rebuild the CSR if served or queried
 void free_serve(abcore_ctx *ctx);
 void free_gfq(abcore_ctx *ctx);
 int serve_components(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
+// the serving loop's re-peel counters summed over targets: regions, region vertices, cascades,
+// cascaded vertices (zeros when not serving; read while the loop runs they may lag)
+void serve_counters(abcore_ctx *ctx, int64_t out[4]);
 
 // components.cu -- connected components (union-find)
 int cc_hook_base(abcore_ctx *ctx, int32_t *parent, const uint32_t *tomb, cudaStream_t st,

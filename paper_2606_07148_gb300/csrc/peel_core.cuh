@@ -595,43 +595,59 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                 e[k] = __ldg(&a.off[x[k] + 1]);
             }
         }
+        bool viol[INIT_ILP];
+        int len[INIT_ILP];
 #pragma unroll
         for (int k = 0; k < INIT_ILP; ++k) {
-            bool viol = false;
-            int nch = 0, len = 0;
+            viol[k] = false;
+            len[k] = 0;
             const bool upper = x[k] >= 0 && x[k] < a.nU;
             if (x[k] >= 0) {
                 const bool hubx = upper ? x[k] < a.hubcutU : x[k] - a.nU < a.hubcutV;
                 if ((upper ? a.searchU : a.searchV) || hubx) {
                     // candidate neighbours form the row's prefix below the other layer's bound
                     const int32_t bound = upper ? a.nU + a.pV : a.pU;
-                    len = e[k] == s[k] ? 0 : row_prefix(a.adj, s[k], e[k], bound, upper ? fracU : fracV, probes);
+                    len[k] = e[k] == s[k] ? 0 : row_prefix(a.adj, s[k], e[k], bound, upper ? fracU : fracV, probes);
                 } else {
-                    len = (int)(e[k] - s[k]);
+                    len[k] = (int)(e[k] - s[k]);
                 }
-                cnt_store(a, x[k], len);
-                a.plen[x[k]] = len;
+                cnt_store(a, x[k], len[k]);
+                a.plen[x[k]] = len[k];
                 inits++;
-                viol = len < (upper ? a.thrU : a.thrV) || known_dead(a, x[k]);
-                nch = len > 0 ? 1 : 0;  // chunk 0; its consumer queues the rest of a long row
+                viol[k] = len[k] < (upper ? a.thrU : a.thrV) || known_dead(a, x[k]);
             }
-            if (a.round0) {
-                // listed for k_round0 instead of queued
-                const unsigned vm = __ballot_sync(ABC_FULL, viol);
-                if (vm) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&a.ctl->l0n, (unsigned long long)__popc(vm));
-                    base = __shfl_sync(ABC_FULL, base, 0);
-                    if (viol) {
+        }
+        if (a.round0) {
+            // listed for k_round0 instead of queued: one reservation on the list's shared counter
+            // for the warp's violators of all INIT_ILP passes
+            unsigned vm[INIT_ILP];
+            int tot = 0;
+#pragma unroll
+            for (int k = 0; k < INIT_ILP; ++k) {
+                vm[k] = __ballot_sync(ABC_FULL, viol[k]);
+                tot += __popc(vm[k]);
+            }
+            if (tot) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&a.ctl->l0n, (unsigned long long)tot);
+                base = __shfl_sync(ABC_FULL, base, 0);
+#pragma unroll
+                for (int k = 0; k < INIT_ILP; ++k) {
+                    if (viol[k]) {
+                        const bool upper = x[k] < a.nU;
                         if (a.fallen != nullptr) mark_fallen(a, x[k], __ldg(&a.new2old[x[k]]));
                         // the row's first entry, length and layer: k_round0 needs nothing more
-                        a.l0[base + __popc(vm & lanemask_lt())] = make_longlong2(s[k], (long long)len | (upper ? L0_UPPER : 0));
+                        a.l0[base + __popc(vm[k] & lanemask_lt())] =
+                            make_longlong2(s[k], (long long)len[k] | (upper ? L0_UPPER : 0));
                         ls.pushes++;
                     }
+                    base += (unsigned long long)__popc(vm[k]);
                 }
-            } else {
-                push_add(a, pb, pc, viol, x[k], nch, ls);
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < INIT_ILP; ++k)
+                push_add(a, pb, pc, viol[k], x[k] < 0 ? 0 : x[k], len[k] > 0 ? 1 : 0, ls);  // chunk 0
         }
     }
     push_flush(a, pb, pc);

@@ -1342,6 +1342,20 @@ static int gfq_query(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alph
     return ABCORE_OK;
 }
 
+void serve_counters(abcore_ctx *ctx, int64_t out[4]) {
+    for (int i = 0; i < 4; ++i) out[i] = 0;
+    ServeState *s = ctx->serve;
+    if (!s) return;
+    for (const TargetDev &T : s->tdev) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        if (cudaMemcpy(h, T.st, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        for (int i = 0; i < 4; ++i) out[i] += (int64_t)h[i];
+    }
+}
+
 int query_edge(abcore_ctx *ctx, int32_t u, int32_t v, int op, int32_t alpha, int32_t beta, uint8_t *in_core) {
     if (ctx->prm.query_scope == 1) return gfq_query(ctx, u, v, op, alpha, beta, in_core);
     if (ctx->gfq) {

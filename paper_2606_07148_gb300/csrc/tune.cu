@@ -72,7 +72,14 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
     const bool batch = (what & ABCORE_TUNE_BATCH) != 0;
     std::vector<Knob> knobs;
     if (batch) {
-        knobs.push_back({"batch_plain_below", {0, 2, 4, 8, 16, 32, 64, 128}});
+        // splits between single peels and chains at the sample's own alphas: none, then below
+        // each of its smallest distinct alphas in turn
+        std::vector<int64_t> split{0};
+        std::vector<int32_t> al(alphas, alphas + n);
+        std::sort(al.begin(), al.end());
+        al.erase(std::unique(al.begin(), al.end()), al.end());
+        for (size_t i = 0; i + 1 < al.size() && i < 6; ++i) split.push_back((int64_t)al[i] + 1);
+        knobs.push_back({"batch_plain_below", split});
         knobs.push_back({"batch_seed", {0, 1}});
         knobs.push_back({"batch_wave", {2, 4, 8, 16}});
         knobs.push_back({"blocks_per_sm", {0, 3}});
