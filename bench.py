@@ -404,6 +404,7 @@ def run_peel(args, rank, world, local):
     torch.cuda.synchronize()
     csr_ms = e0.elapsed_time(e1)
     tuned, tune_s = None, 0.0
+    apply_params(core, args)  # (untuned settings apply to the tuning runs too)
     if not args.no_autotune:
         t = time.perf_counter()
         _, tuned = core.autotune(pairs)

@@ -480,6 +480,11 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         ABC_TRY(abcore_sync(ctx));
         p.packed_counts = (int)value;
         free_batch(ctx);
+    } else if (k == "count_swizzle") {
+        if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "count_swizzle must be 0 or 1");
+        ABC_TRY(abcore_sync(ctx));
+        p.count_swizzle = (int)value;
+        free_batch(ctx);
     } else if (k == "round0_variant") {
         if (value < 0 || value > 4) return ctx->fail(ABCORE_EINVAL, "round0_variant must be 0..4");
         ABC_TRY(abcore_sync(ctx));
@@ -584,6 +589,7 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     else if (k == "packed_counts") *value = p.packed_counts;
     else if (k == "round0") *value = p.round0;
     else if (k == "round0_variant") *value = p.round0_variant;
+    else if (k == "count_swizzle") *value = p.count_swizzle;
     else if (k == "pdl") *value = p.pdl;
     else if (k == "blocks_per_sm") *value = p.blocks_per_sm;
     else if (k == "mode") *value = p.mode;

@@ -72,6 +72,7 @@ struct BatchArgs {
     int32_t chunk;
     int32_t batch_entries, flush_steps;
     int32_t packed;          // 16-bit counts (every degree below 2^16)
+    int32_t swz;             // counts in the swizzled layout (PeelArgs::swz)
     uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     a.adj = B.adj;
     a.cnt = mem.cnt;
     a.packed = B.packed;
+    set_count_layout(a, cd.pU0, cd.pV0, B.swz != 0);  // later steps' candidates are prefixes of these
     a.plen = mem.plen;
     a.q = mem.q;
     a.qcap = B.qcap;
@@ -513,7 +515,11 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
     b->mem.resize(chains);
     for (int c = 0; c < chains; ++c) {
         ChainMem &m = b->mem[c];
-        ABC_TRY(ctx->alloc(&m.cnt, (size_t)(batch_packed(ctx) ? n / 2 + 1 : std::max<int64_t>(n, 1)), "batch counts"));
+        // counts in the swizzled layout need each layer's power-of-two range
+        uint32_t mu = 0, mv = 0;
+        int64_t bv = 0;
+        const int64_t slots = std::max(n, swz_layout(g.nU, g.nV, &mu, &mv, &bv));
+        ABC_TRY(ctx->alloc(&m.cnt, (size_t)(batch_packed(ctx) ? slots / 2 + 1 : std::max<int64_t>(slots, 1)), "batch counts"));
         ABC_TRY(ctx->alloc(&m.plen, (size_t)std::max<int64_t>(n, 1), "batch prefixes"));
         ABC_TRY(ctx->alloc(&m.q, (size_t)qcap, "batch queue"));
         ABC_TRY(ctx->alloc(&m.ctl, 1, "batch control"));
@@ -560,6 +566,9 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.flags = b->flags;
         B.batch_entries = ctx->prm.batch_entries;
         B.packed = batch_packed(ctx) ? 1 : 0;
+        // chains keep counts in vertex order: every step scans all of a chain's candidates in
+        // order, which the swizzled layout would turn into random sector reads (measured slower)
+        B.swz = 0;
         B.flush_steps = ctx->prm.flush_steps;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;

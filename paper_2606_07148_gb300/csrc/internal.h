@@ -48,9 +48,19 @@ constexpr long long L0_UPPER = 1ll << 62;
 struct PeelArgs {
     const int64_t *off;      // [n+1] row offsets, internal unified ids
     const int32_t *adj;      // [2m] neighbours, each row ascending
-    int32_t *cnt;            // [n] count of live candidate neighbours (the atomic target); with
-                             // `packed`, n uint16 counts, two per 32-bit word
+    int32_t *cnt;            // count of live candidate neighbours (the atomic target), one slot per
+                             // vertex (cnt_slot); with `packed`, uint16 counts, two per 32-bit word
     int32_t packed;
+    // count layout: with swz, vertex x's count lives at slot swizzle(x) -- per layer, the odd
+    // multiplicative hash of the layer-local id modulo the power-of-two range just above the
+    // layer's candidate prefix (U slots [0, swz_mask_u], V slots swz_base_v + [0, swz_mask_v]) --
+    // so the counts of the hubs (the lowest ids of the degree-ordered layers, which draw most
+    // decrements) fall on different L2 lines and slices instead of a few neighbouring ones, while
+    // the candidates' counts stay at least half as dense as in vertex order (and in L2); only
+    // candidates' counts are ever touched. Without swz, slot x.
+    int32_t swz;
+    uint32_t swz_mask_u, swz_mask_v;
+    int64_t swz_base_v;
     int32_t *plen;           // [n] row prefix a removed candidate walks (candidate neighbours)
     unsigned long long *q;   // [qcap] work queue of (vertex << 32 | chunk); ~0 = empty slot
     long long qcap;
@@ -122,6 +132,8 @@ struct Params {
                                // decides per workload.
     int round0_variant = 0;    // k_round0's compiled (entries per lane per step, blocks per SM) pair:
                                // 0 (8, any), 1 (4, 8), 2 (16, 4), 3 (8, 8); 4: rows four at a time
+    int count_swizzle = 1;     // single peel: counts in the swizzled layout (see PeelArgs::swz); 0: in
+                               // vertex order (batch chains always keep vertex order)
     int pdl = 1;               // single peel: launch the kernels after the count init as
                                // programmatic dependents of the one before (each waits for its
                                // predecessor on the device; the launch latency overlaps its tail)
@@ -188,7 +200,8 @@ struct SlotInfo {
 
 struct PeelWork {
     int64_t n = 0, qcap = 0;
-    int32_t *cnt = nullptr;        // [n]
+    int32_t *cnt = nullptr;        // [cnt_slots] (each layer's power-of-two range, see PeelArgs::swz)
+    int64_t cnt_slots = 0;
     int32_t *plen = nullptr;       // [n]
     unsigned long long *q = nullptr;
     PeelCtl *ctl = nullptr;        // [CTL_RING] device control blocks
@@ -383,6 +396,29 @@ int community_compute(abcore_ctx *ctx, const uint8_t *d_alive, int32_t q_interna
                       uint8_t *d_mask_v, int64_t *size);
 int cc_emit(abcore_ctx *ctx, int32_t *parent, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp, cudaStream_t st);
 int components_compute(abcore_ctx *ctx, int32_t *d_lab_u, int32_t *d_lab_v, int64_t *ncomp);
+
+// The swizzled count layout of a graph with nU upper and nV lower vertices: per layer a
+// power-of-two slot range (masks), the V range after the U range; returns the slots needed.
+__host__ __device__ static inline int64_t swz_layout(int32_t nU, int32_t nV, uint32_t *mask_u, uint32_t *mask_v,
+                                                     int64_t *base_v) {
+    auto pow2 = [](int32_t k) {
+        uint32_t p = 1;
+        while ((int64_t)p < (int64_t)k) p <<= 1;
+        return p;
+    };
+    const uint32_t su = pow2(nU), sv = pow2(nV);
+    *mask_u = su - 1;
+    *mask_v = sv - 1;
+    *base_v = su;
+    return (int64_t)su + sv;
+}
+
+// Fill a PeelArgs' count layout for candidate prefixes of pU and pV vertices (swizzled when
+// `on`); it fits any count array laid out for the whole layers (swz_layout of nU, nV).
+__host__ __device__ static inline void set_count_layout(PeelArgs &a, int32_t pU, int32_t pV, bool on) {
+    a.swz = on ? 1 : 0;
+    swz_layout(pU, pV, &a.swz_mask_u, &a.swz_mask_v, &a.swz_base_v);
+}
 
 static inline int64_t cnt_ge(const std::vector<int64_t> &t, int32_t thr) {
     if (thr <= 0) return t.empty() ? 0 : t[0];

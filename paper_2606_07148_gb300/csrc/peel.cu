@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
 }
 
 __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
-    if (x < a.nU) return x < a.pU && (x < a.cU || __ldcg(&a.cnt[x]) >= a.thrU);
-    return x < a.nU + a.pV && (x < a.nU + a.cV || __ldcg(&a.cnt[x]) >= a.thrV);
+    if (x < a.nU) return x < a.pU && (x < a.cU || abc::cnt_load(a, x) >= a.thrU);
+    return x < a.nU + a.pV && (x < a.nU + a.cV || abc::cnt_load(a, x) >= a.thrV);
 }
 
 __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
@@ -370,13 +370,18 @@ int peel_prepare(abcore_ctx *ctx) {
     // every vertex is queued at most once, as ceil(row / chunk) items; idle warps may also hold
     // one ticket batch each beyond the last item
     const int64_t qcap = n + (2 * g.m) / std::max(ctx->prm.chunk, 1) + 1024 + (int64_t)ctx->num_sms * 64 * 32;
-    if (w.n == n && w.qcap >= qcap && w.cnt && w.flag_blocks >= cascade_grid(ctx)) {
+    uint32_t mu = 0, mv = 0;
+    int64_t bv = 0;
+    const int64_t slots = std::max(n, swz_layout(g.nU, g.nV, &mu, &mv, &bv));
+    if (w.n == n && w.qcap >= qcap && w.cnt && w.cnt_slots >= slots && w.flag_blocks >= cascade_grid(ctx)) {
         // the round0 list (16 bytes a vertex) is only made once round0 is asked for
         if (ctx->prm.round0 && !w.l0) ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
         return ABCORE_OK;
     }
     free_peel(ctx);
-    ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(n, 1), "peel counts"));
+    // counts in the swizzled layout need each layer's power-of-two range
+    ABC_TRY(ctx->alloc(&w.cnt, (size_t)std::max<int64_t>(slots, 1), "peel counts"));
+    w.cnt_slots = slots;
     ABC_TRY(ctx->alloc(&w.plen, (size_t)std::max<int64_t>(n, 1), "peel prefixes"));
     if (ctx->prm.round0) ABC_TRY(ctx->alloc(&w.l0, (size_t)std::max<int64_t>(n, 1), "initial violators"));
     ABC_TRY(ctx->alloc(&w.q, (size_t)qcap, "peel queue"));
@@ -423,6 +428,7 @@ void free_peel(abcore_ctx *ctx) {
     }
     w.last = -1;
     w.n = w.qcap = 0;
+    w.cnt_slots = 0;
 }
 
 // Launch k on the context's stream; with `pdl`, as a programmatic dependent of the kernel before
@@ -520,6 +526,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.off = g.off;
     a.adj = g.adj;
     a.cnt = w.cnt;
+    set_count_layout(a, pU, pV, ctx->prm.count_swizzle != 0);
     a.plen = w.plen;
     a.q = w.q;
     a.qcap = w.qcap;

@@ -70,22 +70,34 @@ __device__ __forceinline__ bool cand_of(const PeelArgs &a, int32_t y, bool upper
 // half the footprint keeps more of them in L2. A packed decrement subtracts from the word holding
 // the count; a count is never decremented below zero (each decrement stands for a distinct live
 // neighbour falling), so no borrow crosses into the other half.
+// Slot of vertex x's count (PeelArgs::swz): the odd multiplier makes the per-layer map a
+// bijection of the layer's power-of-two range.
+constexpr unsigned long long SWZ_MUL = 0x9E3779B1ull;
+__device__ __forceinline__ int64_t cnt_slot(const PeelArgs &a, int32_t x) {
+    if (!a.swz) return x;
+    if (x < a.nU) return (int64_t)(((unsigned long long)(uint32_t)x * SWZ_MUL) & a.swz_mask_u);
+    return a.swz_base_v + (int64_t)(((unsigned long long)(uint32_t)(x - a.nU) * SWZ_MUL) & a.swz_mask_v);
+}
 __device__ __forceinline__ int cnt_load(const PeelArgs &a, int32_t x) {
-    return a.packed ? (int)__ldcg(reinterpret_cast<const unsigned short *>(a.cnt) + x) : __ldcg(&a.cnt[x]);
+    const int64_t s = cnt_slot(a, x);
+    return a.packed ? (int)__ldcg(reinterpret_cast<const unsigned short *>(a.cnt) + s) : __ldcg(&a.cnt[s]);
 }
 __device__ __forceinline__ void cnt_store(const PeelArgs &a, int32_t x, int v) {
-    if (a.packed) reinterpret_cast<unsigned short *>(a.cnt)[x] = (unsigned short)v;
-    else a.cnt[x] = v;
+    const int64_t s = cnt_slot(a, x);
+    if (a.packed) reinterpret_cast<unsigned short *>(a.cnt)[s] = (unsigned short)v;
+    else a.cnt[s] = v;
 }
 __device__ __forceinline__ int cnt_dec(const PeelArgs &a, int32_t x) {  // returns the old count
-    if (!a.packed) return atomicSub(&a.cnt[x], 1);
-    const unsigned sh = (unsigned)(x & 1) << 4;
-    const unsigned old = atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (x >> 1), 1u << sh);
+    const int64_t s = cnt_slot(a, x);
+    if (!a.packed) return atomicSub(&a.cnt[s], 1);
+    const unsigned sh = (unsigned)(s & 1) << 4;
+    const unsigned old = atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (s >> 1), 1u << sh);
     return (int)((old >> sh) & 0xffffu);
 }
 __device__ __forceinline__ void cnt_dec_noret(const PeelArgs &a, int32_t x) {
-    if (!a.packed) atomicAdd(&a.cnt[x], -1);
-    else atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (x >> 1), 1u << ((unsigned)(x & 1) << 4));
+    const int64_t s = cnt_slot(a, x);
+    if (!a.packed) atomicAdd(&a.cnt[s], -1);
+    else atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (s >> 1), 1u << ((unsigned)(s & 1) << 4));
 }
 
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in

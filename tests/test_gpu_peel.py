@@ -439,3 +439,37 @@ def test_mask_gather_with_and_without_the_removal_bitmap(bitmap_pct):
                     core.compute(a, b, bu[1:], bv[3:])
                     assert np.array_equal(bu[1:].cpu().numpy(), wu) and np.array_equal(bv[3:].cpu().numpy(), wv), ("unaligned", nU, a, b)
         core.close()
+
+
+@pytest.mark.parametrize("swizzle", [0, 1])
+def test_count_layouts_agree_with_the_oracle(swizzle):
+    # counts in vertex order and in the swizzled layout (each layer's ids hashed over its
+    # power-of-two range); layers whose sizes are and are not powers of two; single peels in every
+    # counting mode with and without round0, and batch chains with 16- and 32-bit counts
+    for nU, nV, m, seed in ((4096, 3000, 60_000, 3), (5000, 2048, 50_000, 4)):
+        eu, ev = synth.chung_lu_edges(nU, nV, m, 2.1, 2.3, seed=seed, kmax=300)
+        eu, ev = eu.numpy(), ev.numpy()
+        off, adj = oracle.build_csr(nU, nV, eu, ev)
+        core = ABCore(0)
+        core.set_param("count_swizzle", swizzle)
+        core.load_edges(nU, nV, eu, ev)
+        pairs = [(2, 3), (5, 5), (1, 12), (9, 2), (30, 30)]
+        want = {p: oracle.peel(nU, nV, off, adj, *p) for p in pairs}
+        for mode in (-1, 0, 3):
+            for r0 in (0, 1):
+                core.set_param("mode", mode)
+                core.set_param("round0", r0)
+                for p in pairs:
+                    mu, mv = core.compute(*p)
+                    assert np.array_equal(mu.cpu().numpy(), want[p][0]) and \
+                        np.array_equal(mv.cpu().numpy(), want[p][1]), (swizzle, nU, mode, r0, p)
+        core.set_param("mode", -1)
+        grid = synth.grid_pairs(6, 1, 64)
+        gw = {p: oracle.peel(nU, nV, off, adj, *p) for p in grid}
+        for packed in (1, 0):
+            core.set_param("packed_counts", packed)
+            bu, bv = core.compute_batch([p[0] for p in grid], [p[1] for p in grid])
+            bu, bv = bu.cpu().numpy(), bv.cpu().numpy()
+            for i, p in enumerate(grid):
+                assert np.array_equal(bu[i], gw[p][0]) and np.array_equal(bv[i], gw[p][1]), (swizzle, packed, p)
+        core.close()
