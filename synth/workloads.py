@@ -29,6 +29,10 @@ WORKLOADS = {
     # a (64, 64) query still far beyond the L2
     "profile-20Mx10M-300M": dict(nU=20_000_000, nV=10_000_000, m=300_000_000, gamma_u=2.0,
                                  gamma_v=2.3, seed=3, kmax=None, pairs=[(64, 64)]),
+    # the batch recipe at a fifth of the vertices and of the edges (0.85 GB of CSR, 1.5 GB of
+    # masks): small enough for a profiler that replays each launch many times
+    "batch-4Mx2M-100M": dict(nU=4_000_000, nV=2_000_000, m=100_000_000, gamma_u=2.1, gamma_v=2.2,
+                             seed=2, kmax=None, pairs=grid_pairs(16, 1, 512)),
     # serving: seed 4, 10M x 5M, 200M edges, exponents 2.1 / 2.2, 100k updates
     "serve-10Mx5M-200M": dict(nU=10_000_000, nV=5_000_000, m=200_000_000, gamma_u=2.1,
                               gamma_v=2.2, seed=4, kmax=None, n_ops=100_000,
