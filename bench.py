@@ -716,6 +716,7 @@ def run_batch(args, rank, world, local):
                          % (len(sample), oracle_threads(), wall, csr_s)}
         cpu.update(cpu_info())
         del off, adj
+    rec["roofline"]["traffic"] = traffic_from_profiles("k_batch", args.workload)
     line = {
         "metric": "batched (alpha,beta)-cores/s", "value": round(value, 2), "unit": "cores/s",
         "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
