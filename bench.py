@@ -165,7 +165,7 @@ KERNEL_NAMES = {0: "k_init", 1: "k_stream+k_round0+k_scan", 2: "k_cascade", 3: "
 
 COUNTER_KEYS = ("peels", "candidates", "init_vertices", "search_probes", "stream_entries", "stream_decrements",
                 "scanned", "round0_rows", "entries", "decrements", "pushes", "items", "emit_gathered",
-                "emit_scattered", "mask_zeroed")
+                "emit_scattered", "mask_zeroed", "hub_decrements", "hub_flushes")
 
 
 def algorithmic_bytes(st):
@@ -500,12 +500,16 @@ def run_peel(args, rank, world, local):
         return decs(sa) / (kms / 1e3) if kms > 0 else 0.0
     casc = rate(2, lambda x: x["decrements"] - x["stream_decrements"])
     first = rate(1, lambda x: x["stream_decrements"])
+    # decrements summed in a block's shared-memory hub table reach L2 as one atomic per table entry
+    first_l2 = rate(1, lambda x: x["stream_decrements"] - x["hub_decrements"] + x["hub_flushes"])
     l2_atomics = {"unit": "G/s",
                   "k_cascade": {"decrements_per_s": round(casc / 1e9, 2), "peak_per_s": round(at_ret / 1e9, 2),
                                 "frac": round(casc / at_ret, 4) if at_ret > 0 else None, "returns": True},
                   "k_stream+k_round0+k_scan": {"decrements_per_s": round(first / 1e9, 2),
+                                               "l2_atomics_per_s": round(first_l2 / 1e9, 2),
                                                "peak_per_s": round(at_noret / 1e9, 2),
                                                "frac": round(first / at_noret, 4) if at_noret > 0 else None,
+                                               "l2_frac": round(first_l2 / at_noret, 4) if at_noret > 0 else None,
                                                "returns": False},
                   "probe": "2^26 random atomicSub over a 32 MB int array (L2-resident), abcore_measure_atomics"}
 

@@ -94,6 +94,9 @@ typedef struct {
     int64_t serve_region_vertices; /* vertices in those regions                                 */
     int64_t serve_cascades;  /* served deletes that cascaded inside a target core              */
     int64_t serve_cascade_vertices; /* vertices those cascades removed                          */
+    int64_t hub_decrements;  /* of stream_decrements, those summed in a block's shared-memory hub
+                                table (round0_variant 5) instead of going to L2 one by one      */
+    int64_t hub_flushes;     /* L2 atomics that wrote those tables back to the counts           */
 } abcore_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------------- */

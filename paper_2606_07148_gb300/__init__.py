@@ -262,7 +262,8 @@ class ABCore:
         return int(v.value)
 
     TUNED = ("blocks_per_sm", "chunk", "grab_div", "batch_entries", "flush_steps", "hub_degree", "probe_bytes",
-             "emit_scatter_max_pct", "emit_bitmap_min_pct", "round0", "round0_variant", "batch_wave", "batch_seed", "batch_plain_below")
+             "emit_scatter_max_pct", "emit_bitmap_min_pct", "round0", "round0_variant", "round0_hub", "batch_entries_small",
+             "batch_wave", "batch_seed", "batch_plain_below")
 
     def graph_info(self):
         nU, nV, du, dv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -59,6 +59,7 @@ class abcore_stats(ctypes.Structure):
         ("round0_rows", ctypes.c_int64), ("scope_queries", ctypes.c_int64), ("scope_vertices", ctypes.c_int64),
         ("serve_regions", ctypes.c_int64), ("serve_region_vertices", ctypes.c_int64),
         ("serve_cascades", ctypes.c_int64), ("serve_cascade_vertices", ctypes.c_int64),
+        ("hub_decrements", ctypes.c_int64), ("hub_flushes", ctypes.c_int64),
     ]
 
     def as_dict(self):

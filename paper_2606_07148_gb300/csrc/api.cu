@@ -486,9 +486,14 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         p.count_swizzle = (int)value;
         free_batch(ctx);
     } else if (k == "round0_variant") {
-        if (value < 0 || value > 4) return ctx->fail(ABCORE_EINVAL, "round0_variant must be 0..4");
+        if (value < 0 || value > 5) return ctx->fail(ABCORE_EINVAL, "round0_variant must be 0..5");
         ABC_TRY(abcore_sync(ctx));
         p.round0_variant = (int)value;
+    } else if (k == "round0_hub") {
+        // two layers' tables of ints in one block's shared memory (at most 227 KB)
+        if (value < 0 || value > 28672) return ctx->fail(ABCORE_EINVAL, "round0_hub must be 0..28672");
+        ABC_TRY(abcore_sync(ctx));
+        p.round0_hub = (int)value;
     } else if (k == "pdl") {
         if (value < 0 || value > 1) return ctx->fail(ABCORE_EINVAL, "pdl must be 0 or 1");
         ABC_TRY(abcore_sync(ctx));
@@ -502,6 +507,15 @@ int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value) {
         ABC_TRY(abcore_sync(ctx));
         p.flush_steps = (int)value;
         free_batch(ctx);
+    } else if (k == "batch_entries_small") {
+        if (value != 0 && (value < 128 || value > (1 << 24)))
+            return ctx->fail(ABCORE_EINVAL, "batch_entries_small must be 0 or in [128, 2^24]");
+        ABC_TRY(abcore_sync(ctx));
+        p.batch_entries_small = (int)value;
+    } else if (k == "local_rounds") {
+        if (value < 0 || value > 4096) return ctx->fail(ABCORE_EINVAL, "local_rounds must be 0..4096");
+        ABC_TRY(abcore_sync(ctx));
+        p.local_rounds = (int)value;
     } else if (k == "grab_div") {
         if (value < 0) return ctx->fail(ABCORE_EINVAL, "grab_div must be >= 0");
         p.grab_div = (int)value;
@@ -584,11 +598,14 @@ int abcore_get_param(abcore_ctx *ctx, const char *name, int64_t *value) {
     const std::string k(name);
     if (k == "chunk") *value = p.chunk;
     else if (k == "grab_div") *value = p.grab_div;
+    else if (k == "local_rounds") *value = p.local_rounds;
+    else if (k == "batch_entries_small") *value = p.batch_entries_small;
     else if (k == "batch_entries") *value = p.batch_entries;
     else if (k == "flush_steps") *value = p.flush_steps;
     else if (k == "packed_counts") *value = p.packed_counts;
     else if (k == "round0") *value = p.round0;
     else if (k == "round0_variant") *value = p.round0_variant;
+    else if (k == "round0_hub") *value = p.round0_hub;
     else if (k == "count_swizzle") *value = p.count_swizzle;
     else if (k == "pdl") *value = p.pdl;
     else if (k == "blocks_per_sm") *value = p.blocks_per_sm;

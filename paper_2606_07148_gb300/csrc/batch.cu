@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     }
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
-    (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
+    (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     if (prof) prof[1] = abc::now_ns();
     for (int j = 1; j < cd.nsteps; ++j) {
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
             abc::fall_scan_u(a, smem[wib], t0, nthreads, ls, sc);
         }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
-        (void)abc::cascade_loop(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
+        (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
         if (prof) prof[j + 1] = abc::now_ns();
     }

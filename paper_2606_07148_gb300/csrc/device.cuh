@@ -79,6 +79,23 @@ __device__ __forceinline__ long long warp_sum64(long long v) {
     return v;
 }
 
+// Block-collective: add every thread's v[i] to *dst[i], with one global atomic per counter per
+// block. A launch's thousands of warps finishing at once would otherwise queue on the same few
+// words (same-address atomics are served one at a time).
+template <int N>
+__device__ __forceinline__ void block_add(const unsigned long long (&v)[N], unsigned long long *const (&dst)[N]) {
+    __shared__ unsigned long long s_acc[N];
+    if (threadIdx.x < N) s_acc[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const unsigned long long x = (unsigned long long)warp_sum64((long long)v[i]);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_acc[i], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < N && s_acc[threadIdx.x]) atomicAdd(dst[threadIdx.x], s_acc[threadIdx.x]);
+}
+
 // Record the first error code seen by any thread (0 = none).
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
 

@@ -27,6 +27,9 @@ struct PeelCtl {
     unsigned long long l0n;    // candidates found below their bound by the count init (round0)
     unsigned long long pad4[15];
     unsigned long long st[12]; // stat counters, see ST_* below
+    unsigned long long ph[4];  // with PeelArgs::phases: globaltimer ns at the cascade's start, when
+                               // the last block saw the queue drained, and when the last block
+                               // finished the mask emission
 };
 enum {
     ST_INIT = 0,     // candidate vertices initialised
@@ -39,6 +42,8 @@ enum {
     ST_STEPS = 7,    // chain steps (batch)
     ST_SDECS = 8,    // atomic decrements issued by the violator stream
     ST_SCAN = 9,     // candidates checked after the violator stream
+    ST_HUBDECS = 10, // first-round decrements summed in a block's shared hub table
+    ST_HUBFLUSH = 11, // atomics that wrote those tables' sums back to the counts
 };
 
 // Everything a peel kernel needs, passed by value.
@@ -79,6 +84,13 @@ struct PeelArgs {
     int32_t batch_entries;   // entries one warp walks per batch at most (the rest is re-queued)
     int32_t flush_steps;     // steps a pending push may wait before its warp flushes
     int32_t grab_div;        // queue items per grab = clamp(available / grab_div, 1, 32)
+    int32_t local_rounds = 256; // batches one warp may chain on its own pushes (cascade_loop)
+    int32_t phases = 0;      // 1: k_cascade records its phase times in PeelCtl::ph
+    unsigned long long *trace = nullptr; // diagnostics: the watcher warp samples the queue here
+                                         // instead of taking work (cascade_loop)
+    int32_t batch_entries_small = 0; // > 0: the batch limit of a warp whose grab left the queue
+                                     // nearly empty (fewer than grab_div * 8 items behind it), so
+                                     // that warps with nothing to do take over what it defers
     int32_t searchU;         // 1: U counts by searching U rows; 0: by streaming V violators
     int32_t searchV;         // 1: V counts by searching V rows; 0: by streaming U violators
     int32_t hubcutU;         // U ids below this count by search whatever searchU says (and the
@@ -131,13 +143,17 @@ struct Params {
                                // latency-bound (80M edges, (50,50): 0.30 -> 0.53 ms). The autotuner
                                // decides per workload.
     int round0_variant = 0;    // k_round0's compiled (entries per lane per step, blocks per SM) pair:
-                               // 0 (8, any), 1 (4, 8), 2 (16, 4), 3 (8, 8); 4: rows four at a time
+                               // 0 (8, any), 1 (4, 8), 2 (16, 4), 3 (8, 8); 4: rows four at a time;
+                               // 5: rows four at a time, hub decrements summed in shared memory
+    int round0_hub = 16384;    // variant 5: hub counts per layer kept in each block's table
     int count_swizzle = 1;     // single peel: counts in the swizzled layout (see PeelArgs::swz); 0: in
                                // vertex order (batch chains always keep vertex order)
     int pdl = 1;               // single peel: launch the kernels after the count init as
                                // programmatic dependents of the one before (each waits for its
                                // predecessor on the device; the launch latency overlaps its tail)
     int grab_div = 0;          // 0 = automatic (resident warps / 8)
+    int local_rounds = 256;    // single peel: see PeelArgs::local_rounds
+    int batch_entries_small = 512; // single peel: see PeelArgs::batch_entries_small (0: off)
     int threads = 256;
     int blocks_per_sm = 0;     // 0 = occupancy calculator
     int mode = -1;             // -1 auto; else bit 0 searchU, bit 1 searchV
@@ -194,6 +210,7 @@ constexpr int CTL_RING = 64;  // peels that may be in flight (ABCORE_ASYNC) befo
 struct SlotInfo {
     int64_t cands = 0, n = 0;
     int emit = 0;
+    int32_t alpha = 0, beta = 0;
     bool timed = false, has_init = false, has_stream = false;
     unsigned kinds = 0;  // kernel kinds timed (bit ABCORE_K_*) when timed
 };
@@ -206,6 +223,7 @@ struct PeelWork {
     unsigned long long *q = nullptr;
     PeelCtl *ctl = nullptr;        // [CTL_RING] device control blocks
     PeelCtl *ctl_host = nullptr;   // [CTL_RING] pinned readback
+    unsigned long long *trace = nullptr; // [CTL_RING][TRACE_WORDS] queue samples (log level 2)
     bool pending[CTL_RING] = {};
     SlotInfo info[CTL_RING];
     cudaEvent_t ev[CTL_RING][4] = {};  // created on first timed use: before init, after init,
@@ -251,6 +269,8 @@ struct abcore_ctx {
     int64_t dev_bytes = 0, peak_bytes = 0;
     int cascade_blocks = 0;
     int init_blocks = 0;     // resident k_init blocks (occupancy x SMs)
+    int scan_blocks = 0;     // resident k_scan blocks
+    size_t hub_smem = 0;     // dynamic shared memory k_round0_hub has been allowed so far
     BatchState *batch = nullptr;
     ServeState *serve = nullptr;
     GfqState *gfq = nullptr;   // on-the-fly queries with the component scope (query_scope = 1)

@@ -48,14 +48,9 @@ __global__ void __launch_bounds__(INIT_THREADS, 5) k_init(PeelArgs a) {
     unsigned long long probes = 0, inits = 0;
     abc::init_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls,
                     probes, inits);
-    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)inits);
-    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)probes);
-    unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
-    if ((threadIdx.x & 31) == 0) {
-        if (v0) atomicAdd(&a.ctl->st[ST_INIT], v0);
-        if (v1) atomicAdd(&a.ctl->st[ST_PROBES], v1);
-        if (v2) atomicAdd(&a.ctl->st[ST_PUSHES], v2);
-    }
+    const unsigned long long v[3] = {inits, probes, ls.pushes};
+    unsigned long long *const d[3] = {&a.ctl->st[ST_INIT], &a.ctl->st[ST_PROBES], &a.ctl->st[ST_PUSHES]};
+    abc::block_add<3>(v, d);
 }
 
 __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t sa, int64_t ea, int64_t sb,
@@ -66,14 +61,9 @@ __global__ void __launch_bounds__(STREAM_THREADS) k_stream(PeelArgs a, int64_t s
     unsigned long long ents = 0;
     abc::stream_range(a, sa, ea, sb, eb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                       (int64_t)gridDim.x * blockDim.x, ls, ents);
-    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)ents);
-    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.decs);
-    unsigned long long v2 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
-    if ((threadIdx.x & 31) == 0) {
-        if (v0) atomicAdd(&a.ctl->st[ST_STREAM], v0);
-        if (v1) atomicAdd(&a.ctl->st[ST_SDECS], v1);
-        if (v2) atomicAdd(&a.ctl->st[ST_PUSHES], v2);
-    }
+    const unsigned long long v[3] = {ents, ls.decs, ls.pushes};
+    unsigned long long *const d[3] = {&a.ctl->st[ST_STREAM], &a.ctl->st[ST_SDECS], &a.ctl->st[ST_PUSHES]};
+    abc::block_add<3>(v, d);
 }
 
 __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
@@ -82,13 +72,11 @@ __global__ void __launch_bounds__(256) k_scan(PeelArgs a) {
     abc::grid_dep_wait();
     LaneStats ls;
     unsigned long long scanned = 0;
-    abc::scan_range(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, ls, scanned);
-    unsigned long long v0 = (unsigned long long)abc::warp_sum64((long long)scanned);
-    unsigned long long v1 = (unsigned long long)abc::warp_sum64((long long)ls.pushes);
-    if ((threadIdx.x & 31) == 0) {
-        if (v0) atomicAdd(&a.ctl->st[ST_SCAN], v0);
-        if (v1) atomicAdd(&a.ctl->st[ST_PUSHES], v1);
-    }
+    abc::scan_range<64, true>(a, pbuf[threadIdx.x >> 5], (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                              (int64_t)gridDim.x * blockDim.x, ls, scanned);
+    const unsigned long long v[2] = {scanned, ls.pushes};
+    unsigned long long *const d[2] = {&a.ctl->st[ST_SCAN], &a.ctl->st[ST_PUSHES]};
+    abc::block_add<2>(v, d);
 }
 
 // round0: the rows of the candidates the count init found below their bound (listed in l0 with
@@ -154,26 +142,44 @@ __global__ void __launch_bounds__(256, R0_MINB) k_round0(PeelArgs a) {
         }
         __syncwarp();
     }
-    ents = (unsigned long long)abc::warp_sum64((long long)ents);
-    decs = (unsigned long long)abc::warp_sum64((long long)decs);
-    if (lane == 0) {
-        if (ents) atomicAdd(&a.ctl->st[ST_STREAM], ents);
-        if (decs) atomicAdd(&a.ctl->st[ST_SDECS], decs);
+    const unsigned long long v[2] = {ents, decs};
+    unsigned long long *const d[2] = {&a.ctl->st[ST_STREAM], &a.ctl->st[ST_SDECS]};
+    abc::block_add<2>(v, d);
+}
+
+// One first-round decrement of candidate y. With a hub table (HUB), a decrement of one of the
+// first hU U or hV V candidates -- the highest degrees, since ids follow degree, and so the most
+// frequent targets of the walked rows -- is added to the block's shared-memory tally instead of
+// being sent to L2; the tally goes to the counts once, when the block is done. No crossing is
+// looked for in this round, so only the final counts matter and the order of the subtractions
+// does not.
+template <bool HUB>
+__device__ __forceinline__ void r0_dec(const PeelArgs &a, int32_t y, int *s_hub, int hU, int hV,
+                                       unsigned long long &hub) {
+    if (HUB) {
+        const int k = y < a.nU ? (y < hU ? y : -1) : (y - a.nU < hV ? hU + (y - a.nU) : -1);
+        if (k >= 0) {
+            atomicAdd(&s_hub[k], 1);
+            hub++;
+            return;
+        }
     }
+    abc::cnt_dec_noret(a, y);
 }
 
 // The same walk with the rows taken four at a time by the whole warp: lanes read consecutive
 // entries of one row (coalesced), two 32-entry chunks of each of the four rows in flight, so no
 // entry has to look up its row; lanes past a row's end idle (the rows are short, each below its
-// bound). Rows longer than 64 entries finish in a loop.
-__global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
+// bound). Rows longer than 64 entries finish in a loop. Warp-level body of k_round0_rows and
+// k_round0_hub.
+template <bool HUB>
+__device__ __forceinline__ void round0_rows_walk(const PeelArgs &a, int *s_hub, int hU, int hV,
+                                                 unsigned long long &ents, unsigned long long &decs,
+                                                 unsigned long long &hub) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    abc::grid_dep_launch();
-    abc::grid_dep_wait();
     const int64_t nl0 = (int64_t)a.ctl->l0n;  // written by k_init, earlier on the stream
-    unsigned long long ents = 0, decs = 0;
     longlong2 nxt = make_longlong2(0, 0);
     if (gw * 32 + lane < nl0) nxt = __ldg(&a.l0[gw * 32 + lane]);
     for (int64_t g0 = gw * 32; g0 < nl0; g0 += nw * 32) {
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
                 ents++;
                 int32_t t;
                 if (abc::cand_of(a, y[u], up[u >> 1] != 0, t) && (t > 0 || !a.skip_zero)) {
-                    abc::cnt_dec_noret(a, y[u]);
+                    r0_dec<HUB>(a, y[u], s_hub, hU, hV, hub);
                     decs++;
                 }
             }
@@ -214,19 +220,53 @@ __global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
                     ents++;
                     int32_t t;
                     if (abc::cand_of(a, z, up[k] != 0, t) && (t > 0 || !a.skip_zero)) {
-                        abc::cnt_dec_noret(a, z);
+                        r0_dec<HUB>(a, z, s_hub, hU, hV, hub);
                         decs++;
                     }
                 }
             }
         }
     }
-    ents = (unsigned long long)abc::warp_sum64((long long)ents);
-    decs = (unsigned long long)abc::warp_sum64((long long)decs);
-    if (lane == 0) {
-        if (ents) atomicAdd(&a.ctl->st[ST_STREAM], ents);
-        if (decs) atomicAdd(&a.ctl->st[ST_SDECS], decs);
+}
+
+__device__ __forceinline__ void round0_stats(const PeelArgs &a, unsigned long long ents, unsigned long long decs,
+                                             unsigned long long hub, unsigned long long flushed) {
+    const unsigned long long v[4] = {ents, decs, hub, flushed};
+    unsigned long long *const d[4] = {&a.ctl->st[ST_STREAM], &a.ctl->st[ST_SDECS], &a.ctl->st[ST_HUBDECS],
+                                      &a.ctl->st[ST_HUBFLUSH]};
+    abc::block_add<4>(v, d);
+}
+
+__global__ void __launch_bounds__(256) k_round0_rows(PeelArgs a) {
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
+    unsigned long long ents = 0, decs = 0, hub = 0;
+    round0_rows_walk<false>(a, nullptr, 0, 0, ents, decs, hub);
+    round0_stats(a, ents, decs, 0, 0);
+}
+
+// k_round0_rows with a hub table of hU + hV ints in dynamic shared memory, one 1024-thread block
+// per SM (each block's table costs up to hU + hV atomics when it is written back, so the grid
+// holds as few blocks as keep the SMs full). In degree order a row's first entries are its hub
+// neighbours, and on power-law graphs a few thousand hubs per layer draw a large share of all
+// decrements, which then cost a shared-memory atomic instead of an L2 one.
+__global__ void __launch_bounds__(1024, 1) k_round0_hub(PeelArgs a, int hU, int hV) {
+    extern __shared__ int s_hub[];
+    abc::grid_dep_launch();
+    for (int i = threadIdx.x; i < hU + hV; i += blockDim.x) s_hub[i] = 0;
+    __syncthreads();
+    abc::grid_dep_wait();
+    unsigned long long ents = 0, decs = 0, hub = 0, flushed = 0;
+    round0_rows_walk<true>(a, s_hub, hU, hV, ents, decs, hub);
+    __syncthreads();
+    for (int i = threadIdx.x; i < hU + hV; i += blockDim.x) {
+        const int v = s_hub[i];
+        if (v != 0) {
+            abc::cnt_sub_noret(a, i < hU ? i : a.nU + (i - hU), v);
+            flushed++;
+        }
     }
+    round0_stats(a, ents, decs, hub, flushed);
 }
 
 __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
@@ -234,15 +274,28 @@ __device__ __forceinline__ bool alive_of(const PeelArgs &a, int32_t x) {
     return x < a.nU + a.pV && (x < a.nU + a.cV || abc::cnt_load(a, x) >= a.thrV);
 }
 
-__global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
+__device__ __forceinline__ void k_cascade_emit(const PeelArgs &a, int ok, int64_t gw, int64_t nw, int lane);
+
+__global__ void __launch_bounds__(256, 4) k_cascade(PeelArgs a) {
     __shared__ WarpSmem smem[256 / 32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     abc::grid_dep_wait();
+    if (a.phases && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->ph[0] = abc::now_ns();
     LaneStats ls;
     const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div, blockIdx.x == 0 && wib == 0);
-    abc::flush_stats(a, ls);
+    abc::flush_stats_block(a, ls);
+    if (a.phases && threadIdx.x == 0) atomicMax(&a.ctl->ph[1], (unsigned long long)abc::now_ns());
+    k_cascade_emit(a, ok, gw, nw, lane);
+    if (a.phases) {
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(&a.ctl->ph[2], (unsigned long long)abc::now_ns());
+    }
+}
+
+// The mask emission after the cascade (k_cascade's second phase).
+__device__ __forceinline__ void k_cascade_emit(const PeelArgs &a, int ok, int64_t gw, int64_t nw, int lane) {
     if (!ok || a.emit == 0) return;
     const int64_t n = (int64_t)a.nU + a.nV;
     if (a.emit == 1) {
@@ -333,13 +386,28 @@ __global__ void __launch_bounds__(256) k_cascade(PeelArgs a) {
             }
         }
     } else {
+        // scatter: each lane tests SILP candidates at once (their count loads in flight
+        // together), then looks up the survivors' caller ids and sets their mask bytes
+        constexpr int SILP = 8;
         const int64_t P = (int64_t)a.pU + a.pV;
-        for (int64_t p = gw * 32 + lane; p < P; p += nw * 32) {
-            const int32_t x = p < a.pU ? (int32_t)p : (int32_t)(a.nU + (p - a.pU));
-            if (alive_of(a, x)) {
-                const int32_t o = __ldg(&a.new2old[x]);
-                if (x < a.nU) a.mask_u[o] = 1;
-                else a.mask_v[o] = 1;
+        const int64_t stride = nw * 32;
+        for (int64_t b = gw * 32; b < P; b += stride * SILP) {
+            int32_t x[SILP];
+            bool in[SILP];
+#pragma unroll
+            for (int k = 0; k < SILP; ++k) {
+                const int64_t p = b + k * stride + lane;
+                x[k] = p < a.pU ? (int32_t)p : (int32_t)(a.nU + (p - a.pU));
+                in[k] = p < P && alive_of(a, x[k]);
+            }
+            int32_t o[SILP];
+#pragma unroll
+            for (int k = 0; k < SILP; ++k) o[k] = in[k] ? __ldg(&a.new2old[x[k]]) : 0;
+#pragma unroll
+            for (int k = 0; k < SILP; ++k) {
+                if (!in[k]) continue;
+                if (x[k] < a.nU) a.mask_u[o[k]] = 1;
+                else a.mask_v[o[k]] = 1;
             }
         }
     }
@@ -415,6 +483,7 @@ void free_peel(abcore_ctx *ctx) {
     ctx->release(w.stage);
     ctx->release(w.fallen);
     ctx->release(w.flags);
+    ctx->release(w.trace);
     w.flag_blocks = 0;
     if (w.ctl_host) cudaFreeHost(w.ctl_host);
     w.ctl_host = nullptr;
@@ -431,14 +500,14 @@ void free_peel(abcore_ctx *ctx) {
     w.cnt_slots = 0;
 }
 
-// Launch k on the context's stream; with `pdl`, as a programmatic dependent of the kernel before
+// Launch k on the context's stream with `smem` bytes of dynamic shared memory; with `pdl`, as a programmatic dependent of the kernel before
 // it on the stream (k calls grid_dep_wait before it touches memory).
 template <typename... P, typename... A>
-cudaError_t launch_k(bool pdl, void (*k)(P...), int64_t grid, int block, cudaStream_t st, A... args) {
+cudaError_t launch_k(bool pdl, void (*k)(P...), int64_t grid, int block, cudaStream_t st, size_t smem, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::max<int64_t>(grid, 1));
     cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -542,6 +611,14 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.chunk = std::max(ctx->prm.chunk, 32);
     a.batch_entries = ctx->prm.batch_entries;
     a.flush_steps = ctx->prm.flush_steps;
+    a.local_rounds = ctx->prm.local_rounds;
+    a.batch_entries_small = ctx->prm.batch_entries_small;
+    a.phases = ctx->prm.log_level >= 2 ? 1 : 0;
+    if (ctx->prm.log_level >= 2) {
+        if (!w.trace) ABC_TRY(ctx->alloc(&w.trace, (size_t)CTL_RING * abc::TRACE_WORDS, "queue trace"));
+        a.trace = w.trace + (size_t)slot * abc::TRACE_WORDS;
+        ABC_CU(cudaMemsetAsync(a.trace, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    }
     const int blocks = cascade_grid(ctx);
     a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
     a.searchU = mode & 1;
@@ -571,6 +648,8 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     si.cands = pruned ? Pu : P;
     si.n = n;
     si.emit = a.emit;
+    si.alpha = alpha;
+    si.beta = beta;
     si.kinds = (unsigned)ctx->prm.timing_kinds & ((1u << ABCORE_K_INIT) | (1u << ABCORE_K_STREAM) | (1u << ABCORE_K_CASCADE));
     si.timed = ctx->prm.timing != 0 && si.kinds != 0;
     // events: 0 before the count init, 1 after it, 2 before the cascade, 3 after it; only those
@@ -632,7 +711,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             const int64_t work = ((ea - sa) + (eb - sb)) / 4 + 1;
             const int64_t gs = std::min<int64_t>((work + STREAM_THREADS - 1) / STREAM_THREADS,
                                                  (int64_t)ctx->num_sms * 16);
-            ABC_CU(launch_k(pdl && prev_k, k_stream, gs, STREAM_THREADS, ctx->stream, a, sa, ea, sb, eb));
+            ABC_CU(launch_k(pdl && prev_k, k_stream, gs, STREAM_THREADS, ctx->stream, (size_t)0, a, sa, ea, sb, eb));
             si.has_stream = true;
             ctx->stats.launches++;
         }
@@ -641,11 +720,23 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             // is shorter than the bound)
             const int64_t gr = std::min<int64_t>((Pu + 255) / 256, (int64_t)ctx->num_sms * 16);
             switch (ctx->prm.round0_variant) {
-                case 1: ABC_CU(launch_k(pdl && prev_k, k_round0<4, 8>, gr, 256, ctx->stream, a)); break;
-                case 2: ABC_CU(launch_k(pdl && prev_k, k_round0<16, 4>, gr, 256, ctx->stream, a)); break;
-                case 3: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 8>, gr, 256, ctx->stream, a)); break;
-                case 4: ABC_CU(launch_k(pdl && prev_k, k_round0_rows, gr, 256, ctx->stream, a)); break;
-                default: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 1>, gr, 256, ctx->stream, a)); break;
+                case 1: ABC_CU(launch_k(pdl && prev_k, k_round0<4, 8>, gr, 256, ctx->stream, (size_t)0, a)); break;
+                case 2: ABC_CU(launch_k(pdl && prev_k, k_round0<16, 4>, gr, 256, ctx->stream, (size_t)0, a)); break;
+                case 3: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 8>, gr, 256, ctx->stream, (size_t)0, a)); break;
+                case 4: ABC_CU(launch_k(pdl && prev_k, k_round0_rows, gr, 256, ctx->stream, (size_t)0, a)); break;
+                case 5: {
+                    const int hU = (int)std::min<int64_t>(pU, ctx->prm.round0_hub);
+                    const int hV = (int)std::min<int64_t>(pV, ctx->prm.round0_hub);
+                    const size_t smem = (size_t)(hU + hV) * sizeof(int);
+                    if (ctx->hub_smem < smem) {
+                        ABC_CU(cudaFuncSetAttribute(k_round0_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                        ctx->hub_smem = smem;
+                    }
+                    ABC_CU(launch_k(pdl && prev_k, k_round0_hub, std::min<int64_t>(gr, ctx->num_sms), 1024,
+                                    ctx->stream, smem, a, hU, hV));
+                    break;
+                }
+                default: ABC_CU(launch_k(pdl && prev_k, k_round0<8, 1>, gr, 256, ctx->stream, (size_t)0, a)); break;
             }
             si.has_stream = true;
             ctx->stats.launches++;
@@ -654,8 +745,14 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
             // the candidates these first-round decrements took below their bound
             const int64_t ns = a.round0 ? Pu
                                         : (a.searchU ? 0 : (int64_t)pU - a.hubcutU) + (a.searchV ? 0 : (int64_t)pV - a.hubcutV);
-            const int64_t gsc = std::min<int64_t>((ns + 255) / 256, (int64_t)ctx->num_sms * 16);
-            ABC_CU(launch_k(pdl && prev_k, k_scan, gsc, 256, ctx->stream, a));
+            // at most the blocks that fit at once: fewer blocks, fewer reservations on the queue
+            if (ctx->scan_blocks <= 0) {
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, 256, 0);
+                ctx->scan_blocks = std::max(per_sm, 1) * ctx->num_sms;
+            }
+            const int64_t gsc = std::min<int64_t>((ns + 255) / 256, ctx->scan_blocks);
+            ABC_CU(launch_k(pdl && prev_k, k_scan, gsc, 256, ctx->stream, (size_t)0, a));
             ctx->stats.launches++;
         }
     }
@@ -667,7 +764,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         ABC_CU(cudaEventRecord(w.ev[slot][2], ctx->stream));
         prev_k = false;
     }
-    ABC_CU(launch_k(pdl && prev_k, k_cascade, blocks, 256, ctx->stream, a));
+    ABC_CU(launch_k(pdl && prev_k, k_cascade, blocks, 256, ctx->stream, (size_t)0, a));
     ctx->stats.launches++;
     if (t_casc) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
     ABC_CU(cudaGetLastError());
@@ -683,6 +780,28 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
 
 // Wait for every peel in flight and turn their device status into a return code; the stats
 // describe the most recent one.
+// Log level 2: the cascade's queue over time, from the watcher's samples (time, done, tail,
+// head), about 24 points.
+static void log_queue_trace(abcore_ctx *ctx, const unsigned long long *dev) {
+    std::vector<unsigned long long> h(abc::TRACE_WORDS);
+    if (cudaMemcpy(h.data(), dev, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess) return;
+    const unsigned long long k = std::min<unsigned long long>(h[0], abc::TRACE_SAMPLES);
+    if (k == 0) return;
+    std::string line;
+    const unsigned long long step = std::max<unsigned long long>(1, k / 24);
+    for (unsigned long long i = 0; i < k; i += step) {
+        const unsigned long long *smp = h.data() + 4 + 4 * i;
+        char b[96];
+        snprintf(b, sizeof b, " %.0fus:%llu/%llu/%llu", smp[0] / 1e3, smp[1], smp[2], smp[3]);
+        line += b;
+    }
+    const unsigned long long *last = h.data() + 4 + 4 * (k - 1);
+    char b[96];
+    snprintf(b, sizeof b, " end %.0fus:%llu/%llu", last[0] / 1e3, last[1], last[2]);
+    line += b;
+    ctx->log(2, "cascade queue (time:done/tail/head):%s", line.c_str());
+}
+
 int peel_finish(abcore_ctx *ctx) {
     if (!ctx->pending_async) return ABCORE_OK;
     ctx->pending_async = false;
@@ -708,6 +827,12 @@ int peel_finish(abcore_ctx *ctx) {
         s.pushes += (int64_t)c.st[ST_PUSHES];
         s.items += (int64_t)c.st[ST_ITEMS];
         s.round0_rows += (int64_t)c.l0n;
+        if (c.ph[0] != 0 && c.ph[2] >= c.ph[1] && c.ph[1] >= c.ph[0])
+            ctx->log(2, "peel (%d,%d): cascade queue drained after %.1f us, mask emission %.1f us", si.alpha, si.beta,
+                     (c.ph[1] - c.ph[0]) / 1e3, (c.ph[2] - c.ph[1]) / 1e3);
+        if (ctx->prm.log_level >= 2 && w.trace) log_queue_trace(ctx, w.trace + (size_t)i * abc::TRACE_WORDS);
+        s.hub_decrements += (int64_t)c.st[ST_HUBDECS];
+        s.hub_flushes += (int64_t)c.st[ST_HUBFLUSH];
         if (si.emit == 1) s.emit_gathered += si.n;
         if (si.emit == 2) {
             s.emit_scattered += si.cands;

@@ -23,7 +23,8 @@ constexpr unsigned long long EMPTY = ~0ull;
 // one close flag per block, each on its own 128-byte line
 constexpr int FLAG_STRIDE = 32;
 constexpr int MAX_GRAB = 32;
-constexpr int LOCAL_ROUNDS = 256;  // batches one warp may chain on its own pushes (see cascade_loop)
+constexpr int TRACE_SAMPLES = 2048;  // queue samples kept per traced cascade
+constexpr int TRACE_WORDS = 4 + 4 * TRACE_SAMPLES;
 
 // Per-warp buffer of fallen vertices waiting to be queued (see push_add).
 template <int CAP>
@@ -99,6 +100,12 @@ __device__ __forceinline__ void cnt_dec_noret(const PeelArgs &a, int32_t x) {
     if (!a.packed) atomicAdd(&a.cnt[s], -1);
     else atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (s >> 1), 1u << ((unsigned)(s & 1) << 4));
 }
+// v decrements of x's count at once (v never exceeds the count, as above), no return.
+__device__ __forceinline__ void cnt_sub_noret(const PeelArgs &a, int32_t x, int v) {
+    const int64_t s = cnt_slot(a, x);
+    if (!a.packed) atomicAdd(&a.cnt[s], -v);
+    else atomicSub(reinterpret_cast<unsigned *>(a.cnt) + (s >> 1), (unsigned)v << ((unsigned)(s & 1) << 4));
+}
 
 // Row length that a removed candidate x must still walk: the candidate prefix length kept in
 // plen[x] (the full degree when its layer's counts came from the full rows).
@@ -133,6 +140,47 @@ __device__ __forceinline__ void push_flush(const PeelArgs &a, PushBuf<CAP> &pb, 
         }
     }
     __syncwarp();
+    pc = 0;
+}
+
+// Block-collective push_flush: one atomic on tail reserves the slots of all the block's warps
+// (for kernels whose every warp flushes at the end at about the same time).
+template <int CAP>
+__device__ __forceinline__ void push_flush_block(const PeelArgs &a, PushBuf<CAP> &pb, int &pc) {
+    __shared__ unsigned long long s_qbase;
+    __shared__ int s_wtot[32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    __syncwarp();
+    int mine = 0;
+    for (int i = lane; i < pc; i += 32) mine += pb.n[i];
+    const int incl = warp_incl_scan(mine);
+    const int total = __shfl_sync(ABC_FULL, incl, 31);
+    if (lane == 0) s_wtot[wib] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bt = 0;
+        for (int w = 0; w < nwb; ++w) bt += (unsigned long long)s_wtot[w];
+        unsigned long long b0 = bt ? atomicAdd(&a.ctl->tail, bt) : 0ull;
+        if (bt && b0 + bt > (unsigned long long)a.qcap) {
+            set_error(&a.ctl->err, ABCORE_ENOMEM);
+            b0 = ~0ull;
+        }
+        s_qbase = b0;
+    }
+    __syncthreads();
+    const unsigned long long b0 = s_qbase;
+    if (b0 != ~0ull && total > 0) {
+        unsigned long long pos = b0 + (unsigned long long)(incl - mine);
+        for (int w = 0; w < wib; ++w) pos += (unsigned long long)s_wtot[w];
+        for (int i = lane; i < pc; i += 32) {
+            const unsigned long long hi = (unsigned long long)(uint32_t)pb.y[i] << 32;
+            const int nch = pb.n[i];
+            const unsigned c0 = (unsigned)pb.c[i];
+            for (int c = 0; c < nch; ++c) st_relaxed(&a.q[pos + c], hi | (c0 + (unsigned)c));
+            pos += (unsigned long long)nch;
+        }
+    }
+    __syncthreads();
     pc = 0;
 }
 
@@ -257,8 +305,9 @@ constexpr int ILP = 4;
 // have to read the fallen vertex's row length, one more dependent memory round trip per push.)
 //
 // Pushes still buffered when the batch ends are left in sm.push (pc entries) for the caller.
+template <bool PIPE>
 __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long long it, WarpSmem &sm,
-                                              LaneStats &ls, int &pc) {
+                                              LaneStats &ls, int &pc, int lim) {
     const int lane = threadIdx.x & 31;
     long long start = 0;
     int len = 0, upper = 0, more = 0, c = 0;
@@ -284,9 +333,9 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
         upper = x < a.nU;
     }
     int incl = warp_incl_scan(len);
-    // items past batch_entries (never the first non-empty one) go back to the queue untouched;
+    // items past `lim` entries (never the first non-empty one) go back to the queue untouched;
     // a kept chunk 0 of a long row queues the row's other chunks
-    const bool defer = incl - len >= a.batch_entries && it != EMPTY;
+    const bool defer = incl - len >= lim && it != EMPTY;
     push_add(a, sm.push, pc, defer, x, 1, ls, /*fallen=*/false, /*c0=*/c);
     push_add(a, sm.push, pc, more > 0 && !defer, x, more, ls, /*fallen=*/false, /*c0=*/1);
     if (defer) len = 0;
@@ -300,23 +349,40 @@ __device__ __forceinline__ void process_items(const PeelArgs &a, unsigned long l
     sm.upper[lane] = upper;
     __syncwarp();
     int j = 0, since = 0;
+    // With PIPE (software pipelining), the adjacency entries of step b + 32 * ILP are loaded
+    // before the atomics of step b are issued, so each step waits for one memory round trip
+    // instead of two; it costs registers (kernels already short of them leave it off).
+    int32_t ny[ILP];
+    int32_t nthr[ILP];
+    bool nhit[ILP];
+    auto load_step = [&](int b) {
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const int e = b + 32 * u + lane;
+            nhit[u] = false;
+            ny[u] = 0;
+            nthr[u] = 0;
+            if (e < L) {
+                while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
+                ny[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
+                nthr[u] = sm.upper[j];  // layer of the row, resolved below
+                nhit[u] = true;
+            }
+        }
+    };
+    if (PIPE) load_step(0);
     for (int b = 0; b < L; b += 32 * ILP) {
+        if (!PIPE) load_step(b);
         int32_t y[ILP];
         int32_t thr[ILP];
         bool hit[ILP];
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
-            const int e = b + 32 * u + lane;
-            hit[u] = false;
-            y[u] = 0;
-            thr[u] = 0;
-            if (e < L) {
-                while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
-                y[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
-                thr[u] = sm.upper[j];  // layer of the row, resolved below
-                hit[u] = true;
-            }
+            y[u] = ny[u];
+            thr[u] = nthr[u];
+            hit[u] = nhit[u];
         }
+        if (PIPE && b + 32 * ILP < L) load_step(b + 32 * ILP);
         int old[ILP];
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
@@ -411,17 +477,99 @@ __device__ __forceinline__ void close_queue(const PeelArgs &a) {
 // pushers' atomics need. Every waiting warp still checks the error word, and whether `done`
 // moves, on every 64th idle poll: with no progress for timeout_ns it records ABCORE_ETIMEDOUT and
 // leaves. A watcher that sees an error closes the queue so that everyone leaves promptly.
+template <bool PIPE = true>
 __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, LaneStats &ls, int grab_div,
                                             bool watcher) {
     __shared__ volatile uint32_t s_closed;  // == a.epoch once this block learnt of the close
     const int lane = threadIdx.x & 31;
     const bool leader = (threadIdx.x >> 5) == 0;
     if (threadIdx.x == 0) s_closed = 0;
+    // the block holding a tracing watcher (which takes no work)
+    const int obs = __syncthreads_or(watcher && a.trace != nullptr) ? 1 : 0;
+    // The first grab is one atomic on head for the whole block: at launch every warp would grab
+    // at once, and thousands of atomics on that one word take turns.
+    __shared__ unsigned long long s_base;
+    __shared__ int s_k, s_lim;
+    if (threadIdx.x == 0) {
+        s_k = 0;
+        s_lim = a.batch_entries;
+        const int nwk = (int)(blockDim.x >> 5) - obs;
+        const unsigned long long t = ld_relaxed(&a.ctl->tail);
+        const unsigned long long h = ld_relaxed(&a.ctl->head);
+        if (nwk > 0 && t > h && h < CLOSED) {
+            const unsigned long long kk = (t - h) / (unsigned long long)grab_div;
+            const int k = (int)(kk < 1 ? 1 : (kk > MAX_GRAB ? MAX_GRAB : kk));
+            const unsigned long long total = (unsigned long long)k * (unsigned long long)nwk;
+            const unsigned long long base = atomicAdd(&a.ctl->head, total);
+            if (base < CLOSED) {
+                if (base + total > (unsigned long long)a.qcap) {
+                    set_error(&a.ctl->err, ABCORE_ENOMEM);
+                } else {
+                    s_base = base;
+                    s_k = k;
+                    if (a.batch_entries_small > 0 && t < base + total + (unsigned long long)grab_div * 8ull)
+                        s_lim = a.batch_entries_small;
+                }
+            }
+        }
+    }
     __syncthreads();
+    if (watcher && a.trace != nullptr) {
+        // Diagnostics: the watcher takes no work; its lane 0 samples done, tail and head about
+        // every microsecond (the first TRACE_SAMPLES samples are kept) until the queue drains,
+        // fails or stalls for timeout_ns, then closes it as the watcher would.
+        int verdict = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = now_ns();
+            unsigned long long idle_since = t0, last_done = ~0ull, k = 0;
+            for (;;) {
+                const unsigned long long d = ld_acquire(&a.ctl->done);
+                const unsigned long long tl = ld_acquire(&a.ctl->tail);
+                const unsigned long long h = ld_relaxed(&a.ctl->head);
+                const unsigned long long tn = now_ns();
+                if (k < (unsigned long long)TRACE_SAMPLES) {
+                    unsigned long long *smp = a.trace + 4 + 4 * k;
+                    smp[0] = tn - t0;
+                    smp[1] = d;
+                    smp[2] = tl;
+                    smp[3] = h;
+                }
+                ++k;
+                if (ld_relaxed_i32(&a.ctl->err) != 0) {
+                    verdict = 3;
+                    break;
+                }
+                if (d == tl) {
+                    verdict = 1;
+                    break;
+                }
+                if (d != last_done) {
+                    last_done = d;
+                    idle_since = tn;
+                } else if (tn - idle_since > a.timeout_ns) {
+                    set_error(&a.ctl->err, ABCORE_ETIMEDOUT);
+                    verdict = 3;
+                    break;
+                }
+                __nanosleep(1000);
+            }
+            a.trace[0] = k < (unsigned long long)TRACE_SAMPLES ? k : (unsigned long long)TRACE_SAMPLES;
+        }
+        verdict = __shfl_sync(ABC_FULL, verdict, 0);
+        close_queue(a);
+        if (lane == 0) s_closed = a.epoch;
+        return verdict == 1 ? 1 : 0;
+    }
     const uint32_t *myflag = a.flags + (size_t)blockIdx.x * FLAG_STRIDE;
     unsigned long long idle_since = now_ns(), last_done = ~0ull;
     int st = 2;  // this lane's ticket: 0 waiting, 2 none
+    int lim = a.batch_entries;  // entries per batch, chosen at each grab
     unsigned long long my = 0;
+    if (s_k > 0) {  // this warp's share of the block's first grab
+        my = s_base + (unsigned long long)(((int)(threadIdx.x >> 5) - obs) * s_k + lane);
+        st = lane < s_k ? 0 : 2;
+        lim = s_lim;
+    }
     unsigned sleep_ns = 32;
     unsigned idle_polls = 0;
     for (;;) {
@@ -439,6 +587,12 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
                         k = (int)(kk < 1 ? 1 : (kk > MAX_GRAB ? MAX_GRAB : kk));
                     }
                     base = atomicAdd(&a.ctl->head, (unsigned long long)k);
+                    // little left behind this grab: other warps are likely idle, so keep batches
+                    // short and let them take what this one defers
+                    lim = a.batch_entries;
+                    if (a.batch_entries_small > 0 &&
+                        t < base + (unsigned long long)k + (unsigned long long)grab_div * 8ull)
+                        lim = a.batch_entries_small;
                     if (base >= CLOSED) closed = 1;
                     else if (base + (unsigned long long)k > (unsigned long long)a.qcap) {
                         // tickets past the end of the queue: only an overflowed queue gets here
@@ -456,6 +610,7 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
             }
             base = __shfl_sync(ABC_FULL, base, 0);
             k = __shfl_sync(ABC_FULL, k, 0);
+            lim = __shfl_sync(ABC_FULL, lim, 0);
             my = base + (unsigned long long)lane;
             st = lane < k ? 0 : 2;
         }
@@ -474,14 +629,14 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
             // round trip is most of each level's latency). The batch's slots count as done only
             // after the whole chain, so the queue cannot look drained meanwhile.
             int pc = 0;
-            process_items(a, it, sm, ls, pc);
+            process_items<PIPE>(a, it, sm, ls, pc, lim);
             for (int round = 0; pc > 0; ++round) {
                 unsigned long long nxt = EMPTY;
-                if (round >= LOCAL_ROUNDS || !take_local(sm, pc, nxt)) {
+                if (round >= a.local_rounds || !take_local(sm, pc, nxt)) {
                     push_flush(a, sm.push, pc);
                     break;
                 }
-                process_items(a, nxt, sm, ls, pc);
+                process_items<PIPE>(a, nxt, sm, ls, pc, lim);
             }
             __threadfence();
             __syncwarp();
@@ -727,7 +882,7 @@ __device__ __forceinline__ void stream_range(const PeelArgs &a, int64_t sa, int6
 // After the violator stream: queue the candidates counted by degree whose count fell below
 // their bound (hubs and searched layers were queued by init_range). Warp-collective; `t0` is
 // this thread's index among nthreads.
-template <int CAP>
+template <int CAP, bool BLOCK = false>
 __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, int64_t t0, int64_t nthreads,
                                            LaneStats &ls, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
@@ -770,7 +925,8 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
             push_add(a, pb, pc, viol, x[k] < 0 ? 0 : x[k], nch, ls);
         }
     }
-    push_flush(a, pb, pc);
+    if (BLOCK) push_flush_block(a, pb, pc);
+    else push_flush(a, pb, pc);
 }
 
 // A batch chain's step with a higher V bound (thrV, prefix a.pV), run before its cascade: every
@@ -858,6 +1014,14 @@ __device__ __forceinline__ void fall_scan_u(const PeelArgs &a, WarpSmem &sm, int
         push_add(a, sm.push, pc, fall, x, nch, ls);
     }
     push_flush(a, sm.push, pc);
+}
+
+// Block-collective flush_stats.
+__device__ __forceinline__ void flush_stats_block(const PeelArgs &a, LaneStats &ls) {
+    const unsigned long long v[4] = {ls.entries, ls.decs, ls.pushes, ls.items};
+    unsigned long long *const d[4] = {&a.ctl->st[ST_ENTRIES], &a.ctl->st[ST_DECS], &a.ctl->st[ST_PUSHES],
+                                      &a.ctl->st[ST_ITEMS]};
+    block_add<4>(v, d);
 }
 
 __device__ __forceinline__ void flush_stats(const PeelArgs &a, LaneStats &ls) {

@@ -89,13 +89,15 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
         knobs.push_back({"chunk", {256, 512, 1024, 2048}});
         knobs.push_back({"grab_div", {0, 64, 512}});
         knobs.push_back({"batch_entries", {1024, 4096, 16384}});
+        knobs.push_back({"batch_entries_small", {0, 512, 1024}});
         knobs.push_back({"flush_steps", {1, 4, 16}});
         knobs.push_back({"hub_degree", {0, 64, 256, 1024}});
         knobs.push_back({"probe_bytes", {12, 16, 24, 32, 64}});
         knobs.push_back({"emit_scatter_max_pct", {0, 5, 25}});
         knobs.push_back({"emit_bitmap_min_pct", {0, 50, 101}});
         knobs.push_back({"round0", {0, 1}});
-        knobs.push_back({"round0_variant", {0, 2, 4}});
+        knobs.push_back({"round0_variant", {0, 2, 4, 5}});
+        knobs.push_back({"round0_hub", {8192, 16384, 28672}});
     }
     Timer T;
     uint8_t *mu = nullptr, *mv = nullptr;

@@ -226,6 +226,31 @@ def test_peel_mid_size_power_law():
     core.close()
 
 
+def test_queue_knobs_keep_results_exact():
+    # the cascade's work distribution (grab size, batch limits with and without the short limit
+    # for a warp that drained the queue, chains of local batches, flush cadence) decides who walks
+    # which row when, never the result
+    nU, nV, m = 400_000, 200_000, 8_000_000
+    eu, ev = synth.chung_lu_edges(nU, nV, m, 2.1, 2.4, seed=12, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    want = {p: oracle.peel(nU, nV, off, adj, *p) for p in [(3, 3), (12, 6), (40, 40)]}
+    knobs = [dict(batch_entries=128, batch_entries_small=0, local_rounds=0, grab_div=1, flush_steps=1),
+             dict(batch_entries=4096, batch_entries_small=128, local_rounds=1, grab_div=0, flush_steps=16),
+             dict(batch_entries=16384, batch_entries_small=512, local_rounds=256, grab_div=100000, flush_steps=4),
+             dict(batch_entries=1024, batch_entries_small=4096, local_rounds=8, grab_div=64, flush_steps=4)]
+    for kn in knobs:
+        for k, v in kn.items():
+            core.set_param(k, v)
+        for round0 in (0, 1):
+            core.set_param("round0", round0)
+            for p, (wu, wv) in want.items():
+                mu, mv = core.compute(*p)
+                assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (kn, round0, p)
+    core.close()
+
+
 def test_peel_full_size_4Mx2M_80M():
     """The five single peels at full size, each compared byte for byte with the oracle."""
     spec = synth.WORKLOADS["peel-4Mx2M-80M"]
@@ -282,13 +307,29 @@ def test_round0_first_round_without_returns(mode):
     core.set_param("round0", 1)
     core.set_param("mode", mode)
     pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8), (70, 3), (2, 150)]
-    for variant in range(5):
+    # variant 5 sums hub decrements in shared memory: no table, a table smaller than a warp, one
+    # of a few rows' worth, and one larger than either candidate layer
+    walks = [(v, 16384) for v in range(5)] + [(5, 0), (5, 7), (5, 64), (5, 16384)]
+    sdecs = {}
+    for variant, hub in walks:
         core.set_param("round0_variant", variant)
+        core.set_param("round0_hub", hub)
         for a, b in pairs:
+            core.set_param("reset_stats", 1)
             mu, mv = core.compute(a, b)
+            st = core.stats()
             wu, wv = oracle.peel(nU, nV, off, adj, a, b)
-            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (mode, variant, a, b)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (mode, variant, hub, a, b)
+            # every walk makes the same decrements; only variant 5 with a table sums some of them
+            assert sdecs.setdefault((a, b), st["stream_decrements"]) == st["stream_decrements"], (variant, hub, a, b)
+            assert 0 <= st["hub_flushes"] <= st["hub_decrements"] <= st["stream_decrements"]
+            if variant < 5 or hub == 0:
+                assert st["hub_decrements"] == 0 and st["hub_flushes"] == 0
+            elif hub == 16384 and mode == 3:
+                # a table past both candidate layers holds every first-round target
+                assert st["hub_decrements"] == st["stream_decrements"]
     core.set_param("round0_variant", 0)
+    core.set_param("round0_hub", 16384)
     if mode == 3:
         core.core_numbers()
         core.set_param("algo", 2)
@@ -406,7 +447,7 @@ def test_round0_violator_list_longer_than_the_grid():
         if (a, b) == (4, 4):
             assert n_viol > 2 * lanes, (n_viol, lanes)  # several groups per warp
         wu, wv = oracle.peel(nU, nV, off, adj, a, b)
-        for r0, variant in ((0, 0), (1, 0), (1, 4)):
+        for r0, variant in ((0, 0), (1, 0), (1, 4), (1, 5)):
             core.set_param("round0", r0)
             core.set_param("round0_variant", variant)
             mu, mv = core.compute(a, b)
@@ -473,3 +514,24 @@ def test_count_layouts_agree_with_the_oracle(swizzle):
             for i, p in enumerate(grid):
                 assert np.array_equal(bu[i], gw[p][0]) and np.array_equal(bv[i], gw[p][1]), (swizzle, packed, p)
         core.close()
+
+
+def test_log_level_2_queue_trace_keeps_results(capfd):
+    # at log level 2 the cascade's watcher warp samples the queue instead of taking work and the
+    # phase times are logged; the masks stay exact
+    nU, nV, m = 400_000, 200_000, 8_000_000
+    eu, ev = synth.chung_lu_edges(nU, nV, m, 2.1, 2.4, seed=13, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, _np(eu), _np(ev))
+    core.set_param("log_level", 2)
+    for round0 in (0, 1):
+        core.set_param("round0", round0)
+        for a, b in [(3, 3), (25, 25)]:
+            mu, mv = core.compute(a, b)
+            wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+            assert np.array_equal(mu.cpu().numpy(), wu) and np.array_equal(mv.cpu().numpy(), wv), (round0, a, b)
+    core.set_param("log_level", 0)
+    core.close()
+    err = capfd.readouterr().err
+    assert "cascade queue drained after" in err and "cascade queue (time:done/tail/head)" in err
