@@ -286,11 +286,19 @@ __global__ void __launch_bounds__(256, 4) k_cascade(PeelArgs a) {
     LaneStats ls;
     const int ok = abc::cascade_loop(a, smem[wib], ls, a.grab_div, blockIdx.x == 0 && wib == 0);
     abc::flush_stats_block(a, ls);
-    if (a.phases && threadIdx.x == 0) atomicMax(&a.ctl->ph[1], (unsigned long long)abc::now_ns());
+    if (a.phases && threadIdx.x == 0) {
+        const unsigned long long t = abc::now_ns();
+        atomicMax(&a.ctl->ph[1], t);
+        if (a.trace && blockIdx.x < abc::TRACE_BLOCKS) a.trace[4 + 4 * abc::TRACE_SAMPLES + 2 * blockIdx.x] = t;
+    }
     k_cascade_emit(a, ok, gw, nw, lane);
     if (a.phases) {
         __syncthreads();
-        if (threadIdx.x == 0) atomicMax(&a.ctl->ph[2], (unsigned long long)abc::now_ns());
+        if (threadIdx.x == 0) {
+            const unsigned long long t = abc::now_ns();
+            atomicMax(&a.ctl->ph[2], t);
+            if (a.trace && blockIdx.x < abc::TRACE_BLOCKS) a.trace[4 + 4 * abc::TRACE_SAMPLES + 2 * blockIdx.x + 1] = t;
+        }
     }
 }
 
@@ -617,7 +625,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     if (ctx->prm.log_level >= 2) {
         if (!w.trace) ABC_TRY(ctx->alloc(&w.trace, (size_t)CTL_RING * abc::TRACE_WORDS, "queue trace"));
         a.trace = w.trace + (size_t)slot * abc::TRACE_WORDS;
-        ABC_CU(cudaMemsetAsync(a.trace, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        ABC_CU(cudaMemsetAsync(a.trace, 0, abc::TRACE_WORDS * sizeof(unsigned long long), ctx->stream));
     }
     const int blocks = cascade_grid(ctx);
     a.grab_div = ctx->prm.grab_div > 0 ? ctx->prm.grab_div : std::max(1, blocks * (256 / 32) / 8);
@@ -800,6 +808,21 @@ static void log_queue_trace(abcore_ctx *ctx, const unsigned long long *dev) {
     snprintf(b, sizeof b, " end %.0fus:%llu/%llu", last[0] / 1e3, last[1], last[2]);
     line += b;
     ctx->log(2, "cascade queue (time:done/tail/head):%s", line.c_str());
+    // blocks' cascade exit and emission end, from the watcher's start: quantiles
+    std::vector<double> ex, em;
+    const unsigned long long *blk = h.data() + 4 + 4 * abc::TRACE_SAMPLES;
+    for (int i = 0; i < abc::TRACE_BLOCKS; ++i) {
+        if (blk[2 * i] >= h[1] && h[1] != 0) ex.push_back((blk[2 * i] - h[1]) / 1e3);
+        if (blk[2 * i + 1] >= h[1] && h[1] != 0) em.push_back((blk[2 * i + 1] - h[1]) / 1e3);
+    }
+    auto q = [](std::vector<double> &v, double f) {
+        if (v.empty()) return 0.0;
+        std::sort(v.begin(), v.end());
+        return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1)))];
+    };
+    if (!ex.empty())
+        ctx->log(2, "cascade blocks (%zu): exit us min %.0f med %.0f p90 %.0f max %.0f; emission end min %.0f med %.0f p90 %.0f max %.0f",
+                 ex.size(), q(ex, 0), q(ex, 0.5), q(ex, 0.9), q(ex, 1), q(em, 0), q(em, 0.5), q(em, 0.9), q(em, 1));
 }
 
 int peel_finish(abcore_ctx *ctx) {

@@ -24,7 +24,9 @@ constexpr unsigned long long EMPTY = ~0ull;
 constexpr int FLAG_STRIDE = 32;
 constexpr int MAX_GRAB = 32;
 constexpr int TRACE_SAMPLES = 2048;  // queue samples kept per traced cascade
-constexpr int TRACE_WORDS = 4 + 4 * TRACE_SAMPLES;
+constexpr int TRACE_BLOCKS = 2048;   // blocks whose exit and emission end times are kept
+// header (sample count, watcher start ns), samples, then per block: cascade exit, emission end
+constexpr int TRACE_WORDS = 4 + 4 * TRACE_SAMPLES + 2 * TRACE_BLOCKS;
 
 // Per-warp buffer of fallen vertices waiting to be queued (see push_add).
 template <int CAP>
@@ -521,6 +523,7 @@ __device__ __forceinline__ int cascade_loop(const PeelArgs &a, WarpSmem &sm, Lan
         int verdict = 0;
         if (lane == 0) {
             const unsigned long long t0 = now_ns();
+            a.trace[1] = t0;
             unsigned long long idle_since = t0, last_done = ~0ull, k = 0;
             for (;;) {
                 const unsigned long long d = ld_acquire(&a.ctl->done);
@@ -778,10 +781,10 @@ __device__ __forceinline__ void init_range(const PeelArgs &a, PushBuf<CAP> &pb, 
                 } else {
                     len[k] = (int)(e[k] - s[k]);
                 }
+                viol[k] = len[k] < (upper ? a.thrU : a.thrV) || known_dead(a, x[k]);
                 cnt_store(a, x[k], len[k]);
                 a.plen[x[k]] = len[k];
                 inits++;
-                viol[k] = len[k] < (upper ? a.thrU : a.thrV) || known_dead(a, x[k]);
             }
         }
         if (a.round0) {
