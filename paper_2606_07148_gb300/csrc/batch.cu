@@ -33,6 +33,9 @@ using abc::WarpSmem;
 constexpr int BATCH_THREADS = 256;
 constexpr int MAX_CHAINS_PER_WAVE = 32;
 constexpr int MAX_STEPS = 255;
+// timeline of one chain (log level 2): its start, then three marks per step
+constexpr int PROF_STRIDE = 1 + 3 * MAX_STEPS;
+__host__ __device__ constexpr int prof_at(int step, int phase) { return 1 + 3 * step + phase; }
 
 struct ChainDev {
     int32_t alpha;
@@ -76,12 +79,17 @@ struct BatchArgs {
     uint32_t *flags;
     long long qcap;
     unsigned long long timeout_ns;
-    // optional timeline: prof[c * (MAX_STEPS + 2) + j] = globaltimer when chain c's block 0 starts
+    // optional timeline: prof[c * PROF_STRIDE + 0] = globaltimer when chain c's block 0 starts,
+    // then per step j three marks (prof_at): after its V walk (step 0: the count init), after its
+    // U scan (step 0: the first round), after its cascade
     // (j = 0) and when its step j - 1 has closed (j >= 1); nullptr: not recorded
     unsigned long long *prof;
 };
 
-__global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
+// Compiled for two occupancies: three blocks an SM (80 registers a thread, some spilled) or two
+// (no spills); "blocks_per_sm" = 2 picks the second.
+template <int MINB>
+__global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
     __shared__ WarpSmem smem[BATCH_THREADS / 32];
     int c = 0;
     while (c + 1 < B.nchains && (int)blockIdx.x >= B.chains[c + 1].first_block) ++c;
@@ -133,11 +141,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
     LaneStats ls;
     unsigned long long probes = 0, inits = 0, ents = 0, sdecs = 0;
 
-    unsigned long long *prof = B.prof != nullptr && r == 0 && threadIdx.x == 0 ? B.prof + (size_t)c * (MAX_STEPS + 2)
+    unsigned long long *prof = B.prof != nullptr && r == 0 && threadIdx.x == 0 ? B.prof + (size_t)c * PROF_STRIDE
                                                                                : nullptr;
     if (prof) prof[0] = abc::now_ns();
     abc::init_range(a, smem[wib].push, t0, nthreads, ls, probes, inits);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+    if (prof) prof[prof_at(0, 0)] = abc::now_ns();
     if (cd.ea > cd.sa || cd.eb > cd.sb) {
         const unsigned long long d0 = ls.decs;
         abc::stream_range(a, cd.sa, cd.ea, cd.sb, cd.eb, t0, nthreads, ls, ents);
@@ -148,11 +157,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
         abc::scan_range(a, smem[wib].push, t0, nthreads, ls, scanned);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
     }
+    if (prof) prof[prof_at(0, 1)] = abc::now_ns();
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
     (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
-    if (prof) prof[1] = abc::now_ns();
+    if (prof) prof[prof_at(0, 2)] = abc::now_ns();
     for (int j = 1; j < cd.nsteps; ++j) {
         const int32_t prev = a.thrV;
         const int32_t pv_prev = a.pV;
@@ -175,14 +185,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs B) {
             sdecs += d0;
         }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        if (prof) prof[prof_at(j, 0)] = abc::now_ns();
         {
             unsigned long long sc = 0;
             abc::fall_scan_u(a, smem[wib], t0, nthreads, ls, sc);
         }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
+        if (prof) prof[prof_at(j, 1)] = abc::now_ns();
         (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
-        if (prof) prof[j + 1] = abc::now_ns();
+        if (prof) prof[prof_at(j, 2)] = abc::now_ns();
     }
 out:
     abc::flush_stats(a, ls);
@@ -228,6 +240,35 @@ __global__ void __launch_bounds__(256) k_batch_emit(const int32_t *__restrict__ 
     }
     __syncthreads();
     const int64_t n = (int64_t)nU + nV;
+    if (lvl_stride == 4 && (nU & 3) == 0 && (nV & 3) == 0 &&
+        ((reinterpret_cast<uintptr_t>(masks_u) | reinterpret_cast<uintptr_t>(masks_v)) & 3) == 0) {
+        // four consecutive caller ids per thread (16-byte id load, one 4-byte store per pair), and
+        // each vertex's removal steps in one 4-byte row (at most four chains a wave)
+        const int4 *o4 = reinterpret_cast<const int4 *>(old2new);
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = 4 * q;
+            const int4 xv = __ldg(&o4[q]);
+            const int32_t xs[4] = {xv.x, xv.y, xv.z, xv.w};
+            const bool upper = i < nU;  // nU is a multiple of four: the quad is in one layer
+            uint32_t rows[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) rows[j] = __ldg(reinterpret_cast<const uint32_t *>(lvl + (size_t)xs[j] * 4));
+            for (int p = 0; p < npairs; ++p) {
+                const int ch = pc[p];
+                const unsigned sh = 8u * (unsigned)col[ch];
+                uint32_t bytes = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool cand = upper ? (xs[j] < pU0[ch]) : (xs[j] - nU < pv[p]);
+                    const bool in = cand && (int)((rows[j] >> sh) & 0xffu) > ps[p];
+                    bytes |= (in ? 1u : 0u) << (8 * j);
+                }
+                if (upper) *reinterpret_cast<uint32_t *>(masks_u + (size_t)pi[p] * nU + i) = bytes;
+                else *reinterpret_cast<uint32_t *>(masks_v + (size_t)pi[p] * nV + (i - nU)) = bytes;
+            }
+        }
+        return;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t x = __ldg(&old2new[i]);
         const bool upper = i < nU;
@@ -284,7 +325,7 @@ struct BatchState {
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    unsigned long long *prof = nullptr;  // [waves x MAX_CHAINS_PER_WAVE x (MAX_STEPS + 2)] (log level 2)
+    unsigned long long *prof = nullptr;  // [waves x MAX_CHAINS_PER_WAVE x PROF_STRIDE] (log level 2)
 };
 
 static void destroy_plan(abcore_ctx *ctx, BatchState *b) {
@@ -330,9 +371,13 @@ void free_batch(abcore_ctx *ctx) {
     ctx->batch = nullptr;
 }
 
+static void (*batch_kernel(abcore_ctx *ctx))(BatchArgs) {
+    return ctx->prm.blocks_per_sm == 2 ? k_batch<2> : k_batch<3>;
+}
+
 static int batch_grid(abcore_ctx *ctx) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(ctx), BATCH_THREADS, 0);
     if (ctx->prm.blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->prm.blocks_per_sm);
     return std::max(per_sm, 1) * ctx->num_sms;
 }
@@ -477,7 +522,7 @@ static int make_plan(abcore_ctx *ctx, BatchState *b, int32_t n, const int32_t *a
     }
     ABC_CU(cudaMallocHost(&b->ctl_host, sizeof(PeelCtl) * MAX_CHAINS_PER_WAVE * b->waves.size()));
     if (ctx->prm.log_level >= 2)
-        ABC_TRY(ctx->alloc(&b->prof, b->waves.size() * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2), "batch timeline"));
+        ABC_TRY(ctx->alloc(&b->prof, b->waves.size() * MAX_CHAINS_PER_WAVE * PROF_STRIDE, "batch timeline"));
     ctx->log(1, "batch plan: %d pairs, %d chains in %d waves of up to %d, grid %d blocks, %d seeded chains", n, C,
              (int)b->waves.size(), per_wave, grid, seeded);
     return ABCORE_OK;
@@ -572,7 +617,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         B.flush_steps = ctx->prm.flush_steps;
         B.qcap = b->qcap;
         B.timeout_ns = (unsigned long long)ctx->prm.timeout_ms * 1000000ull;
-        B.prof = b->prof ? b->prof + wi * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2) : nullptr;
+        B.prof = b->prof ? b->prof + wi * MAX_CHAINS_PER_WAVE * PROF_STRIDE : nullptr;
         void *args[] = {&B};
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(w.grid);
@@ -583,7 +628,7 @@ static int enqueue_batch(abcore_ctx *ctx, BatchState *b, uint8_t *d_mu, uint8_t 
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        ABC_CU(cudaLaunchKernelExC(&cfg, (const void *)k_batch, args));
+        ABC_CU(cudaLaunchKernelExC(&cfg, (const void *)batch_kernel(ctx), args));
         ctx->stats.launches++;
         if (!w.pairs.empty()) {
             const int np = (int)w.pairs.size();
@@ -714,20 +759,24 @@ int batch_compute(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32
     if (b->prof && ctx->prm.log_level >= 2) {
         // per chain: the wave, alpha, and each step's duration in microseconds (step 0 includes
         // the count init and the first round)
-        std::vector<unsigned long long> h(b->waves.size() * MAX_CHAINS_PER_WAVE * (MAX_STEPS + 2));
+        std::vector<unsigned long long> h(b->waves.size() * MAX_CHAINS_PER_WAVE * PROF_STRIDE);
         if (cudaMemcpy(h.data(), b->prof, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) == cudaSuccess) {
             for (size_t wi = 0; wi < b->waves.size(); ++wi)
                 for (size_t c = 0; c < b->waves[wi].chains.size(); ++c) {
                     const ChainDev &cd = b->waves[wi].chains[c];
-                    const unsigned long long *t = h.data() + (wi * MAX_CHAINS_PER_WAVE + c) * (MAX_STEPS + 2);
+                    const unsigned long long *t = h.data() + (wi * MAX_CHAINS_PER_WAVE + c) * PROF_STRIDE;
                     std::string line;
-                    char tmp[32];
+                    char tmp[64];
+                    unsigned long long prev = t[0];
                     for (int j = 0; j < cd.nsteps; ++j) {
-                        snprintf(tmp, sizeof(tmp), " %.1f", (double)(t[j + 1] - t[j]) / 1e3);
+                        const unsigned long long a0 = t[prof_at(j, 0)], a1 = t[prof_at(j, 1)], a2 = t[prof_at(j, 2)];
+                        snprintf(tmp, sizeof(tmp), " %.0f/%.0f/%.0f", (double)(a0 - prev) / 1e3, (double)(a1 - a0) / 1e3,
+                                 (double)(a2 - a1) / 1e3);
                         line += tmp;
+                        prev = a2;
                     }
-                    ctx->log(2, "batch wave %zu chain alpha=%d blocks=%d total %.1f us; steps:%s", wi, cd.alpha,
-                             cd.nblocks, (double)(t[cd.nsteps] - t[0]) / 1e3, line.c_str());
+                    ctx->log(2, "batch wave %zu chain alpha=%d blocks=%d total %.1f us; steps (walk/scan/cascade us):%s", wi,
+                             cd.alpha, cd.nblocks, (double)(t[prof_at(cd.nsteps - 1, 2)] - t[0]) / 1e3, line.c_str());
                 }
         }
     }

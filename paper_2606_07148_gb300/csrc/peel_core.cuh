@@ -945,54 +945,69 @@ __device__ __forceinline__ void fall_walk_v(const PeelArgs &a, WarpSmem &sm, int
                                             bool by_lvl, int64_t t0, int64_t nthreads, LaneStats &ls,
                                             unsigned long long &ents, unsigned long long &decs) {
     const int lane = threadIdx.x & 31;
-    for (int64_t b = t0 - lane; b < pv_prev; b += nthreads) {
-        const int64_t i = b + lane;
-        const int32_t x = (int32_t)(a.nU + (i < pv_prev ? i : 0));
-        bool fall = false;
-        int len = 0;
-        long long s = 0;
-        if (i < pv_prev) {
-            const int c = cnt_load(a, x);
-            const bool live = by_lvl ? chain_alive(a, x) : c >= prev_thrV;
-            fall = live && (c < a.thrV || (a.seed_col >= 0 && known_dead(a, x)));
-            if (fall) {
-                a.lvl[(size_t)x * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
-                ls.pushes++;
-                if (c > 0) {
-                    len = __ldcg(&a.plen[x]);
-                    s = __ldg(&a.off[x]);
-                }
-            }
-        }
-        const int incl = warp_incl_scan(len);
-        const int L = __shfl_sync(ABC_FULL, incl, 31);
-        if (L == 0) continue;
-        sm.start[lane] = s;
-        sm.excl[lane] = incl - len;
-        __syncwarp();
-        int j = 0;
-        for (int e0 = 0; e0 < L; e0 += 32 * ILP) {
-            int32_t y[ILP];
+    // WILP groups of 32 vertices per warp per pass: all their count loads are issued first (one
+    // vertex at a time would leave every lane waiting on a load per vertex), then each group's
+    // falling rows are walked in turn
+    constexpr int WILP = 4;
+    for (int64_t b0 = t0 - lane; b0 < pv_prev; b0 += nthreads * WILP) {
+        int cg[WILP];
 #pragma unroll
-            for (int u = 0; u < ILP; ++u) {
-                const int e = e0 + 32 * u + lane;
-                y[u] = -1;
-                if (e < L) {
-                    while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
-                    y[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < ILP; ++u) {
-                if (y[u] < 0) continue;
-                ents++;
-                if (y[u] < a.pU && y[u] >= a.cU) {  // a U candidate
-                    cnt_dec_noret(a, y[u]);
-                    decs++;
-                }
-            }
+        for (int k = 0; k < WILP; ++k) {
+            const int64_t i = b0 + lane + k * nthreads;
+            cg[k] = i < pv_prev ? cnt_load(a, (int32_t)(a.nU + i)) : 0;
         }
-        __syncwarp();
+#pragma unroll 1
+        for (int k = 0; k < WILP; ++k) {
+            const int64_t b = b0 + k * nthreads;  // warp-uniform
+            if (b >= pv_prev) break;
+            const int64_t i = b + lane;
+            const int32_t x = (int32_t)(a.nU + (i < pv_prev ? i : 0));
+            bool fall = false;
+            int len = 0;
+            long long s = 0;
+            if (i < pv_prev) {
+                const int c = cg[k];
+                const bool live = by_lvl ? chain_alive(a, x) : c >= prev_thrV;
+                fall = live && (c < a.thrV || (a.seed_col >= 0 && known_dead(a, x)));
+                if (fall) {
+                    a.lvl[(size_t)x * a.lvl_stride + a.lvl_col] = (uint8_t)a.step;
+                    ls.pushes++;
+                    if (c > 0) {
+                        len = __ldcg(&a.plen[x]);
+                        s = __ldg(&a.off[x]);
+                    }
+                }
+            }
+            const int incl = warp_incl_scan(len);
+            const int L = __shfl_sync(ABC_FULL, incl, 31);
+            if (L == 0) continue;
+            sm.start[lane] = s;
+            sm.excl[lane] = incl - len;
+            __syncwarp();
+            int j = 0;
+            for (int e0 = 0; e0 < L; e0 += 32 * ILP) {
+                int32_t y[ILP];
+#pragma unroll
+                for (int u = 0; u < ILP; ++u) {
+                    const int e = e0 + 32 * u + lane;
+                    y[u] = -1;
+                    if (e < L) {
+                        while (j + 1 < 32 && sm.excl[j + 1] <= e) ++j;
+                        y[u] = ld_adj(&a.adj[sm.start[j] + (e - sm.excl[j])]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < ILP; ++u) {
+                    if (y[u] < 0) continue;
+                    ents++;
+                    if (y[u] < a.pU && y[u] >= a.cU) {  // a U candidate
+                        cnt_dec_noret(a, y[u]);
+                        decs++;
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -1002,19 +1017,29 @@ __device__ __forceinline__ void fall_scan_u(const PeelArgs &a, WarpSmem &sm, int
                                             LaneStats &ls, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
     int pc = 0;
-    for (int64_t b = t0 - lane; b < a.pU; b += nthreads) {
-        const int64_t i = b + lane;
-        const int32_t x = (int32_t)(i < a.pU ? i : 0);
-        bool fall = false;
-        int nch = 0;
-        if (i < a.pU && i >= a.cU) {
-            scanned++;
-            if (cnt_load(a, x) < a.thrU && chain_alive(a, x)) {
-                fall = true;
-                nch = __ldcg(&a.plen[x]) > 0 ? 1 : 0;  // chunk 0 (see process_items)
-            }
+    // FILP vertices per lane per pass: their count loads, then the few removal-step loads, are in
+    // flight together (one vertex at a time leaves every lane waiting on two dependent loads)
+    constexpr int FILP = 8;
+    for (int64_t b = t0 - lane; b < a.pU; b += nthreads * FILP) {
+        int32_t x[FILP];
+        int c[FILP];
+#pragma unroll
+        for (int k = 0; k < FILP; ++k) {
+            const int64_t i = b + lane + k * nthreads;
+            x[k] = (i < a.pU && i >= a.cU) ? (int32_t)i : -1;
+            c[k] = x[k] >= 0 ? cnt_load(a, x[k]) : 0;
         }
-        push_add(a, sm.push, pc, fall, x, nch, ls);
+        bool fall[FILP];
+#pragma unroll
+        for (int k = 0; k < FILP; ++k) fall[k] = x[k] >= 0 && c[k] < a.thrU && chain_alive(a, x[k]);
+        int nch[FILP];
+#pragma unroll
+        for (int k = 0; k < FILP; ++k) nch[k] = (fall[k] && __ldcg(&a.plen[x[k]]) > 0) ? 1 : 0;  // chunk 0
+#pragma unroll
+        for (int k = 0; k < FILP; ++k) {
+            if (x[k] >= 0) scanned++;
+            push_add(a, sm.push, pc, fall[k], x[k] < 0 ? 0 : x[k], nch[k], ls);
+        }
     }
     push_flush(a, sm.push, pc);
 }

@@ -82,7 +82,7 @@ int autotune(abcore_ctx *ctx, int32_t n, const int32_t *alphas, const int32_t *b
         knobs.push_back({"batch_plain_below", split});
         knobs.push_back({"batch_seed", {0, 1}});
         knobs.push_back({"batch_wave", {2, 4, 8, 16}});
-        knobs.push_back({"blocks_per_sm", {0, 3}});
+        knobs.push_back({"blocks_per_sm", {0, 2, 3}});
         knobs.push_back({"chunk", {512, 1024, 2048}});
     } else {
         knobs.push_back({"blocks_per_sm", {0, 3, 2}});

@@ -183,3 +183,28 @@ def test_batch_small_alphas_left_to_single_peels(small, below):
     _check_batch(core, nU, nV, off, adj, pairs)
     _check_batch(core, nU, nV, off, adj, pairs)
     core.close()
+
+
+@pytest.mark.parametrize("nU, nV", [(4000, 3000), (4001, 2999), (4002, 3002)])
+def test_batch_emit_widths(nU, nV):
+    # the masks are written four caller ids at a time when both layers' sizes are multiples of
+    # four (and the wave's removal steps fit one 4-byte row), else one id at a time
+    eu, ev = synth.chung_lu_edges(nU, nV, 40_000, 2.2, 2.3, seed=nU + nV)
+    off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+    _check_batch(core, nU, nV, off, adj, synth.grid_pairs(5, 1, 40))
+    core.close()
+
+
+@pytest.mark.parametrize("per_sm", [2, 3])
+def test_batch_kernel_occupancies(per_sm):
+    # the batch kernel is compiled for two and for three blocks an SM; both give the same masks
+    nU, nV, m = 400_000, 200_000, 8_000_000
+    eu, ev = synth.chung_lu_edges(nU, nV, m, 2.1, 2.2, seed=15, device="cuda")
+    core = ABCore(0)
+    core.load_edges(nU, nV, eu, ev)
+    off, adj = oracle.build_csr(nU, nV, eu.cpu().numpy(), ev.cpu().numpy())
+    core.set_param("blocks_per_sm", per_sm)
+    _check_batch(core, nU, nV, off, adj, synth.grid_pairs(6, 1, 512))
+    core.close()
