@@ -57,6 +57,7 @@ struct ChainMem {
     unsigned long long *q;
     PeelCtl *ctl;
     unsigned *bar;           // group barrier: [0] arrivals, [32] generation
+    uint32_t *ulive;         // bitmap over the U prefix: candidates a step's U scan must look at
 };
 
 struct BatchArgs {
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
         if (prof) prof[prof_at(j, 0)] = abc::now_ns();
         {
             unsigned long long sc = 0;
-            abc::fall_scan_u(a, smem[wib], t0, nthreads, ls, sc);
+            abc::fall_scan_u(a, smem[wib], t0, nthreads, ls, sc, mem.ulive, j == 1);
         }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         if (prof) prof[prof_at(j, 1)] = abc::now_ns();
@@ -361,6 +362,7 @@ void free_batch(abcore_ctx *ctx) {
         ctx->release(m.q);
         ctx->release(m.ctl);
         ctx->release(m.bar);
+        ctx->release(m.ulive);
     }
     ctx->release(b->d_mem);
     ctx->release(b->lvl);
@@ -547,6 +549,7 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
         ctx->release(m.q);
         ctx->release(m.ctl);
         ctx->release(m.bar);
+        ctx->release(m.ulive);
     }
     b->mem.clear();
     ctx->release(b->d_mem);
@@ -564,7 +567,9 @@ static int ensure_memory(abcore_ctx *ctx, BatchState *b, int want_chains) {
         uint32_t mu = 0, mv = 0;
         int64_t bv = 0;
         const int64_t slots = std::max(n, swz_layout(g.nU, g.nV, &mu, &mv, &bv));
-        ABC_TRY(ctx->alloc(&m.cnt, (size_t)(batch_packed(ctx) ? slots / 2 + 1 : std::max<int64_t>(slots, 1)), "batch counts"));
+        // (32 slots of padding: the U scan reads whole 32-vertex words of counts)
+        ABC_TRY(ctx->alloc(&m.cnt, (size_t)(batch_packed(ctx) ? slots / 2 + 17 : slots + 32), "batch counts"));
+        ABC_TRY(ctx->alloc(&m.ulive, (size_t)(g.nU / 32 + 1), "batch live U bitmap"));
         ABC_TRY(ctx->alloc(&m.plen, (size_t)std::max<int64_t>(n, 1), "batch prefixes"));
         ABC_TRY(ctx->alloc(&m.q, (size_t)qcap, "batch queue"));
         ABC_TRY(ctx->alloc(&m.ctl, 1, "batch control"));

@@ -1012,33 +1012,75 @@ __device__ __forceinline__ void fall_walk_v(const PeelArgs &a, WarpSmem &sm, int
 }
 
 // After fall_walk_v: every U candidate that was live (lvl unset) and whose count is now below
-// alpha falls, queued for the cascade. Warp-collective; `t0` is warp-aligned.
+// alpha falls, queued for the cascade. Each lane takes the 32 candidates of one word of `live`, a
+// bitmap over the U prefix: with `full` every candidate of the prefix, else only those whose bit
+// is set. The word is rewritten to hold the ones whose count still meets alpha (a fallen vertex's
+// count stays below alpha, so the bits left set cover every live vertex, and later scans skip the
+// rest). The 32 counts come in 16-byte loads (vertex order, which batch chains keep); a removal
+// step is read only for a count below alpha. A U vertex live at a step has a live neighbour
+// inside the step-0 V prefix, so its row prefix is never empty: it is queued as one item.
+// Warp-collective; `t0` is warp-aligned; the count array holds at least 32 slots past the prefix.
 __device__ __forceinline__ void fall_scan_u(const PeelArgs &a, WarpSmem &sm, int64_t t0, int64_t nthreads,
-                                            LaneStats &ls, unsigned long long &scanned) {
+                                            LaneStats &ls, unsigned long long &scanned, uint32_t *live, bool full) {
     const int lane = threadIdx.x & 31;
     int pc = 0;
-    // FILP vertices per lane per pass: their count loads, then the few removal-step loads, are in
-    // flight together (one vertex at a time leaves every lane waiting on two dependent loads)
-    constexpr int FILP = 8;
-    for (int64_t b = t0 - lane; b < a.pU; b += nthreads * FILP) {
-        int32_t x[FILP];
-        int c[FILP];
-#pragma unroll
-        for (int k = 0; k < FILP; ++k) {
-            const int64_t i = b + lane + k * nthreads;
-            x[k] = (i < a.pU && i >= a.cU) ? (int32_t)i : -1;
-            c[k] = x[k] >= 0 ? cnt_load(a, x[k]) : 0;
+    const int64_t nwords = ((int64_t)a.pU + 31) >> 5;
+    for (int64_t w = t0; w - lane < nwords; w += nthreads) {
+        uint32_t bits = 0;
+        if (w < nwords) {
+            if (full) {
+                const int64_t x0 = w << 5;
+                const int64_t lo = max((int64_t)a.cU - x0, (int64_t)0), hi = min((int64_t)a.pU - x0, (int64_t)32);
+                bits = lo >= hi ? 0u : ((hi == 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u));
+            } else {
+                bits = __ldcg(&live[w]);
+            }
         }
-        bool fall[FILP];
+        uint32_t low = 0;
+        if (bits != 0u) {
+            // the word's 32 counts: 64 bytes (16-bit counts) or 128 bytes
+            int c[32];
+            if (a.packed) {
+                const uint4 *p4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned short *>(a.cnt) + (w << 5));
 #pragma unroll
-        for (int k = 0; k < FILP; ++k) fall[k] = x[k] >= 0 && c[k] < a.thrU && chain_alive(a, x[k]);
-        int nch[FILP];
+                for (int v = 0; v < 4; ++v) {
+                    const uint4 q = __ldcg(&p4[v]);
+                    const uint32_t h[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < FILP; ++k) nch[k] = (fall[k] && __ldcg(&a.plen[x[k]]) > 0) ? 1 : 0;  // chunk 0
+                    for (int t = 0; t < 4; ++t) {
+                        c[8 * v + 2 * t] = (int)(h[t] & 0xffffu);
+                        c[8 * v + 2 * t + 1] = (int)(h[t] >> 16);
+                    }
+                }
+            } else {
+                const int4 *p4 = reinterpret_cast<const int4 *>(a.cnt + (w << 5));
 #pragma unroll
-        for (int k = 0; k < FILP; ++k) {
-            if (x[k] >= 0) scanned++;
-            push_add(a, sm.push, pc, fall[k], x[k] < 0 ? 0 : x[k], nch[k], ls);
+                for (int v = 0; v < 8; ++v) {
+                    const int4 q = __ldcg(&p4[v]);
+                    c[4 * v] = q.x;
+                    c[4 * v + 1] = q.y;
+                    c[4 * v + 2] = q.z;
+                    c[4 * v + 3] = q.w;
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                if (((bits >> b) & 1u) && c[b] < a.thrU) low |= 1u << b;
+            scanned += (unsigned long long)__popc(bits);
+        }
+        // of those below alpha, the ones still live fall now
+        uint32_t fallm = 0;
+        if (low != 0u) {
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                if (((low >> b) & 1u) && chain_alive(a, (int32_t)((w << 5) + b))) fallm |= 1u << b;
+        }
+        if (w < nwords && (full || low != 0u)) live[w] = bits & ~low;
+        while (__ballot_sync(ABC_FULL, fallm != 0u)) {
+            const bool has = fallm != 0u;
+            const int32_t x = has ? (int32_t)((w << 5) + (__ffs(fallm) - 1)) : 0;
+            push_add(a, sm.push, pc, has, x, 1, ls);
+            fallm &= fallm - 1u;
         }
     }
     push_flush(a, sm.push, pc);
