@@ -185,10 +185,11 @@ def algorithmic_bytes(st):
     alg[2] = 24 * removed + 4 * st["entries"] + 8 * dec_casc + st["emit_gathered"] + st.get("mask_zeroed", 0)
     # the queue moves 36 B per item (slot write, read and reset, offset, row length) against 24 B
     # per removed vertex; the gather reads 4 B of caller-order id and 1/4 B of bitmap per vertex,
-    # and each removal sets its bit (8 B); the scatter reads 4 B of count per candidate
+    # and each removal sets its bit (8 B); the scatter reads 4 B of count per candidate, and its
+    # survivor bitmap is read and cleared by the expansion (1/4 B per vertex)
     over[2] = (max(36 * st["items"] - 24 * removed, 0)
                + (4.25 * st["emit_gathered"] + 8 * removed if st["emit_gathered"] > 0 else 0)
-               + 4 * st["emit_scattered"])
+               + 4 * st["emit_scattered"] + st.get("mask_zeroed", 0) / 4)
     return alg, over
 
 

@@ -78,7 +78,7 @@ typedef struct {
     int64_t items;           /* cascade work items (row chunks) processed                      */
     int64_t emit_gathered;   /* mask bytes written by a gather over every vertex               */
     int64_t emit_scattered;  /* candidates checked by a scatter of survivors into zeroed masks */
-    int64_t mask_zeroed;     /* mask bytes cleared before a scatter                            */
+    int64_t mask_zeroed;     /* mask bytes written from the survivor bitmap after a scatter    */
     int64_t launches;        /* kernels launched                                               */
     int64_t kernel_launches[ABCORE_K_KINDS];  /* timed launches per kernel kind                */
     double kernel_ms[ABCORE_K_KINDS];         /* device milliseconds per kernel kind           */

@@ -123,6 +123,9 @@ struct PeelArgs {
     // removes, set when the cascade takes a fallen vertex's first chunk (round0: when the count
     // init lists it) and read, then cleared, by the caller-order mask gather
     uint32_t *fallen;
+    // scatter emission: a bitmap over caller ids (same layout) in which the cascade's last phase
+    // sets the survivors' bits; k_expand writes both masks from it and clears it
+    uint32_t *sbits;
     // queue closing: flag line of block b at flags[b * 32]; the watcher writes `epoch` (nonzero,
     // new for every cascade) into the lines of blocks [flag_first, flag_first + flag_count)
     uint32_t *flags;
@@ -270,6 +273,7 @@ struct abcore_ctx {
     int cascade_blocks = 0;
     int init_blocks = 0;     // resident k_init blocks (occupancy x SMs)
     int scan_blocks = 0;     // resident k_scan blocks
+    int expand_blocks = 0;   // resident k_expand blocks
     size_t hub_smem = 0;     // dynamic shared memory k_round0_hub has been allowed so far
     BatchState *batch = nullptr;
     ServeState *serve = nullptr;

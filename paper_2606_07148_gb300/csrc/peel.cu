@@ -395,7 +395,7 @@ __device__ __forceinline__ void k_cascade_emit(const PeelArgs &a, int ok, int64_
         }
     } else {
         // scatter: each lane tests SILP candidates at once (their count loads in flight
-        // together), then looks up the survivors' caller ids and sets their mask bytes
+        // together), then looks up the survivors' caller ids and sets their bits
         constexpr int SILP = 8;
         const int64_t P = (int64_t)a.pU + a.pV;
         const int64_t stride = nw * 32;
@@ -414,8 +414,43 @@ __device__ __forceinline__ void k_cascade_emit(const PeelArgs &a, int ok, int64_
 #pragma unroll
             for (int k = 0; k < SILP; ++k) {
                 if (!in[k]) continue;
-                if (x[k] < a.nU) a.mask_u[o[k]] = 1;
-                else a.mask_v[o[k]] = 1;
+                // the survivor's bit in the caller-order bitmap (k_expand writes the masks)
+                const uint32_t u = (uint32_t)(x[k] < a.nU ? o[k] : a.nU + o[k]);
+                atomicOr(&a.sbits[u >> 5], 1u << (u & 31));
+            }
+        }
+    }
+}
+
+// After a scatter: both masks from the survivor bitmap, 32 caller ids (one word) per thread
+// and iteration, written as two 16-byte stores where the word's ids lie in one layer and the
+// destination is aligned (else byte by byte); every word is cleared for the next peel. Streaming
+// stores of all n mask bytes replace a memset of the masks and random byte stores.
+__global__ void __launch_bounds__(256) k_expand(PeelArgs a) {
+    abc::grid_dep_launch();
+    abc::grid_dep_wait();
+    const int64_t n = (int64_t)a.nU + a.nV, nw = (n + 31) / 32;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t bits = __ldcg(&a.sbits[w]);
+        if (bits != 0u) a.sbits[w] = 0u;
+        const int64_t i0 = w * 32;
+        // 4 bits -> 4 bytes of 0/1: the multiplier moves bit t to bit 8t, and nothing else lands
+        // on those four positions
+        uint32_t q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = (((bits >> (4 * k)) & 0xfu) * 0x00204081u) & 0x01010101u;
+        uint8_t *dst = nullptr;
+        if (i0 + 32 <= a.nU) dst = a.mask_u + i0;
+        else if (i0 >= a.nU && i0 + 32 <= n) dst = a.mask_v + (i0 - a.nU);
+        if (dst != nullptr && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            __stcs(&d4[0], make_uint4(q[0], q[1], q[2], q[3]));
+            __stcs(&d4[1], make_uint4(q[4], q[5], q[6], q[7]));
+        } else {
+            for (int j = 0; j < 32 && i0 + j < n; ++j) {
+                const uint8_t v = (uint8_t)((bits >> j) & 1u);
+                if (i0 + j < a.nU) a.mask_u[i0 + j] = v;
+                else a.mask_v[i0 + j - a.nU] = v;
             }
         }
     }
@@ -643,6 +678,7 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     a.emit = (d_mask_u == nullptr && d_mask_v == nullptr) ? 0 : (scatter ? 2 : 1);
     a.skip_zero = 1;
     a.fallen = (a.emit == 1 && P * 100 >= (int64_t)ctx->prm.emit_bitmap_min_pct * n) ? w.fallen : nullptr;
+    a.sbits = a.emit == 2 ? w.fallen : nullptr;  // the gather's bitmap is free in a scatter
     a.round0 = (ctx->prm.round0 && w.l0 && (a.searchU || a.searchV)) ? 1 : 0;
     a.l0 = w.l0;
     a.flags = w.flags;
@@ -673,13 +709,9 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
         w.q_dirty = false;
     }
     ABC_CU(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), ctx->stream));
-    if (a.fallen != nullptr && w.fallen_dirty) {
+    if ((a.fallen != nullptr || a.sbits != nullptr) && w.fallen_dirty) {
         ABC_CU(cudaMemsetAsync(w.fallen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1), ctx->stream));
         w.fallen_dirty = false;
-    }
-    if (a.emit == 2) {
-        if (nU) ABC_CU(cudaMemsetAsync(d_mask_u, 0, (size_t)nU, ctx->stream));
-        if (nV) ABC_CU(cudaMemsetAsync(d_mask_v, 0, (size_t)nV, ctx->stream));
     }
     if (t_init) ABC_CU(cudaEventRecord(w.ev[slot][0], ctx->stream));
     // the kernels after the count init follow it as programmatic dependents, except right after
@@ -774,6 +806,16 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     }
     ABC_CU(launch_k(pdl && prev_k, k_cascade, blocks, 256, ctx->stream, (size_t)0, a));
     ctx->stats.launches++;
+    if (a.emit == 2) {
+        if (ctx->expand_blocks <= 0) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand, 256, 0);
+            ctx->expand_blocks = std::max(per_sm, 1) * ctx->num_sms;
+        }
+        const int64_t ge = std::min<int64_t>(((n + 31) / 32 + 255) / 256, ctx->expand_blocks);
+        ABC_CU(launch_k(pdl, k_expand, ge, 256, ctx->stream, (size_t)0, a));
+        ctx->stats.launches++;
+    }
     if (t_casc) ABC_CU(cudaEventRecord(w.ev[slot][3], ctx->stream));
     ABC_CU(cudaGetLastError());
     ABC_CU(cudaMemcpyAsync(w.ctl_host + slot, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, ctx->stream));

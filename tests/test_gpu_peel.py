@@ -535,3 +535,29 @@ def test_log_level_2_queue_trace_keeps_results(capfd):
     core.close()
     err = capfd.readouterr().err
     assert "cascade queue drained after" in err and "cascade queue (time:done/tail/head)" in err
+
+
+def test_mask_scatter_through_the_survivor_bitmap():
+    # the scatter sets survivors' bits in a caller-order bitmap and k_expand writes every mask
+    # byte from it: 16-byte stores where a word's 32 ids lie in one layer and the destination is
+    # aligned, byte stores across the layer boundary, at odd offsets and in the last partial word;
+    # stale bytes in the caller's buffers are overwritten, and the bitmap is clean for the next peel
+    for nU, nV, seed in [(4000, 3008, 21), (4001, 2999, 22), (31, 5, 23)]:
+        m = min(40000, nU * nV // 2)
+        eu, ev = synth.chung_lu_edges(nU, nV, m, 2.2, 2.3, seed=seed)
+        off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
+        core = ABCore(0)
+        core.load_edges(nU, nV, eu.cuda(), ev.cuda())
+        core.set_param("emit_scatter_max_pct", 100)
+        for r0 in (0, 1):
+            core.set_param("round0", r0)
+            for a, b in [(1, 1), (3, 2), (5, 5), (9, 2), (40, 40), (0, 0)]:
+                wu, wv = oracle.peel(nU, nV, off, adj, a, b)
+                for pad_u, pad_v in [(0, 0), (1, 3), (16, 7)]:
+                    bu = torch.full((nU + pad_u,), 7, dtype=torch.uint8, device="cuda")
+                    bv = torch.full((nV + pad_v,), 7, dtype=torch.uint8, device="cuda")
+                    core.compute(a, b, bu[pad_u:], bv[pad_v:])
+                    assert np.array_equal(bu[pad_u:].cpu().numpy(), wu), (nU, r0, a, b, pad_u)
+                    assert np.array_equal(bv[pad_v:].cpu().numpy(), wv), (nV, r0, a, b, pad_v)
+                    assert int(bu[:pad_u].ne(7).sum()) == 0 and int(bv[:pad_v].ne(7).sum()) == 0
+        core.close()
