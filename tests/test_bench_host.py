@@ -60,10 +60,12 @@ def test_algorithmic_bytes_per_kernel_kind():
     # gather's id and bitmap reads (4.25 B a vertex) and the removal bits (8 B a removal)
     assert alg[2] == 24 * 4 + 4 * 50 + 8 * 30 + 64
     assert over[2] == (36 * 5 - 24 * 4) + 4.25 * 64 + 8 * 4
+    # a scatter: 4 B of count per candidate, and the survivor bitmap read and cleared by the
+    # expansion that writes the 64 mask bytes (1/8 B each way per vertex)
     st.update(emit_gathered=0, emit_scattered=9, mask_zeroed=64)
     alg, over = bench.algorithmic_bytes(st)
     assert alg[2] == 24 * 4 + 4 * 50 + 8 * 30 + 64
-    assert over[2] == (36 * 5 - 24 * 4) + 4 * 9
+    assert over[2] == (36 * 5 - 24 * 4) + 4 * 9 + 64 / 4
 
 
 def test_sampled_grid_pairs_cover_corners_and_chain_ends():
