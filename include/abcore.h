@@ -292,14 +292,55 @@ int abcore_serve_stop(abcore_ctx *ctx);
 /* Accumulated counters (see abcore_stats) and the context's device memory. */
 int abcore_get_stats(abcore_ctx *ctx, abcore_stats *out);
 
-/* Set a tuning parameter by name (see the implementation for the list); EINVAL if unknown.
- * Among them: "timing" (1: CUDA events around the launches, summed into abcore_stats.kernel_ms),
- * "timing_kinds" (single peel: bit ABCORE_K_* set for each kernel kind timed; default 0xff --
- * an event between two kernels costs the step about as much as a launch), "pdl" (1, default:
- * the single peel's kernels after the count init launch as programmatic dependents),
- * "emit_bitmap_min_pct" (0, default: the caller-order mask gather tests removal in a bitmap
- * that each removal sets; a query with fewer candidates than this percentage of the vertices
- * reads each candidate's count instead). Results never depend on these parameters. */
+/* Set a parameter by name; EINVAL if the name is unknown or the value out of range. Results
+ * never depend on any of them (except the actions and "query_scope", which picks an equivalent
+ * algorithm). Defaults in brackets; abcore_autotune sets the starred ones.
+ *
+ * Single peel:
+ *   "algo" [0]          0 auto, 1 GCC (plain peel, Algorithm 1), 2 GCC+ (pruned by core numbers,
+ *                       Algorithm 2; needs abcore_core_numbers first); auto takes GCC+ when it leaves
+ *                       fewer vertices than GCC.
+ *   "mode" [-1]         per-layer count init: -1 cost model, 0..3 bit 0 U by row search, bit 1 V.
+ *   "hub_degree"* [256] rows of at least this degree always count by search (0: none).
+ *   "probe_bytes"* [32] the cost model's price of a search probe (steers search vs stream).
+ *   "round0"* [0]       1: walk the initial violators' rows with no-return decrements first.
+ *   "round0_variant"* [0] that walk's form: 0..3 lane-per-entry (entries in flight / blocks an SM:
+ *                       8/any, 4/8, 16/4, 8/8), 4 four rows per warp, 5 the same in one 1024-thread
+ *                       block per SM summing hub decrements in shared memory.
+ *   "round0_hub"* [16384] hubs per layer in variant 5's table (0..28672).
+ *   "count_swizzle" [1] counts in the per-layer multiplicative slot order (0: vertex order).
+ *   "pdl" [1]           later kernels launch as programmatic dependents of the one before.
+ *   "emit_scatter_max_pct"* [5] scatter the survivors when the candidates are at most this
+ *                       percentage of the vertices, else gather over caller ids.
+ *   "emit_bitmap_min_pct"* [0] the gather tests removal in a bitmap when the candidates are at
+ *                       least this percentage of the vertices (101: never; by count instead).
+ * Cascade (single peel; chunk, grab_div, batch_entries and flush_steps also in batch chains):
+ *   "blocks_per_sm"* [0] resident blocks an SM for the cascade and the batch (0: as many as fit;
+ *                       batch: 2 selects the batch kernel compiled for two blocks an SM).
+ *   "chunk"* [1024]     adjacency entries per work item (32..2^20).
+ *   "grab_div"* [0]     queue items per grab = backlog / grab_div, 1..32 (0: resident warps / 8).
+ *   "batch_entries"* [1024] entries a warp walks per batch (128..2^24; the rest is re-queued).
+ *   "batch_entries_small"* [512] the limit when a warp's grab leaves the queue nearly empty (0 off).
+ *   "local_rounds" [256] batches a warp may chain on its own pushes (0..4096).
+ *   "flush_steps"* [4]  steps a buffered push may wait before its warp flushes.
+ * Batch:
+ *   "batch_wave"* [4]   chains per wave (0..32; 0: all at once).
+ *   "batch_plain_below"* [0] pairs with alpha below this run as single peels, not chains.
+ *   "batch_seed"* [0]   1: seed each chain from the finished chain of the next smaller alpha.
+ *   "packed_counts" [1] chains keep 16-bit counts whenever every degree fits.
+ * Serving and queries:
+ *   "serve_inserts" [2^20] initial inserted-edge pool per target (1..2^29; grows on demand).
+ *   "query_scope" [0]   abcore_query_edge re-peels 0 the certificate-bounded region, 1 the
+ *                       endpoints' connected components (the paper's scope).
+ * Diagnostics and limits:
+ *   "timeout_ms" [4000] limit of every bounded device wait, in milliseconds (>= 1).
+ *   "timing" [0]        1: CUDA events around each launch, summed into abcore_stats.kernel_ms.
+ *   "timing_kinds" [0xff] single peel: bit ABCORE_K_* set for each kind timed (an event between two
+ *                       kernels costs the step about as much as a launch).
+ *   "log_level" [0 or ABCORE_LOG] 0 none, 1 plans and events, 2 also timelines (on stderr).
+ *   "debug_stall_slots" [0] test hook: reserve this many queue slots that nothing fills, so the
+ *                       next cascade's bounded wait expires (reported as ABCORE_ETIMEDOUT).
+ * Actions (no value to read back): "reset_stats" zeroes abcore_stats' counters. */
 int abcore_set_param(abcore_ctx *ctx, const char *name, int64_t value);
 
 /* Throughput of random 32-bit atomicSub on this device, per second, with the old value returned

@@ -63,3 +63,18 @@ def test_errors_without_a_context(lib_path):
     assert abi.abcore_destroy(None) == 0
     assert abi.abcore_last_error(None) == b""
     assert abi.abcore_compute(None, 1, 1, None, None, 0) == abi.ABCORE_EINVAL
+
+
+def test_header_documents_every_parameter():
+    # abcore_set_param's comment in the header lists every name the library accepts
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "abcore.h")) as f:
+        header = f.read()
+    block = header[header.index("/* Set a parameter by name"):header.index("int abcore_set_param(")]
+    documented = set(re.findall(r'"([a-z0-9_]+)"', block))
+    with open(os.path.join(root, "paper_2606_07148_gb300", "csrc", "api.cu")) as f:
+        api = f.read()
+    accepted = set(re.findall(r'k == "([a-z0-9_]+)"', api))
+    assert accepted, "no parameter names found in the implementation"
+    assert accepted == documented, (sorted(accepted - documented), sorted(documented - accepted))
