@@ -92,6 +92,7 @@ struct BatchArgs {
 template <int MINB>
 __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
     __shared__ WarpSmem smem[BATCH_THREADS / 32];
+    __shared__ unsigned s_hubs[abc::WALK_HUBS];  // the V walk's U-hub tallies (fall_walk_v)
     int c = 0;
     while (c + 1 < B.nchains && (int)blockIdx.x >= B.chains[c + 1].first_block) ++c;
     const ChainDev cd = B.chains[c];
@@ -99,6 +100,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
     const int G = cd.nblocks;
     const int r = (int)blockIdx.x - cd.first_block;
     const int wib = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < abc::WALK_HUBS; i += blockDim.x) s_hubs[i] = 0u;
+    // (init_range's first barrier orders these stores before any walk)
 
     PeelArgs a{};
     a.off = B.off;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
         a.frac_rows = B.fracs[cd.beta_off + j];
         {
             unsigned long long e0 = 0, d0 = 0;
-            abc::fall_walk_v(a, smem[wib], pv_prev, prev, a.dead_own != 0, t0, nthreads, ls, e0, d0);
+            abc::fall_walk_v(a, smem[wib], pv_prev, prev, a.dead_own != 0, t0, nthreads, ls, e0, d0, s_hubs);
             ents += e0;
             sdecs += d0;
         }

@@ -941,9 +941,16 @@ __device__ __forceinline__ void scan_range(const PeelArgs &a, PushBuf<CAP> &pb, 
 // count is 0 has no live neighbour left and walks nothing. With `by_lvl` a V vertex is live iff
 // its lvl is unset (seeded chains queue known-dead vertices whatever their count); otherwise iff
 // its count meets the previous bound prev_thrV. Warp-collective; `t0` is warp-aligned.
+// Block-collective when `tab` is set: decrements of the first WALK_HUBS U ids (the U hubs: ids
+// follow degree, and a row's first entries are its hub neighbours) go to the block's shared tally
+// `tab`, added to the counts (and the tally zeroed) once the block's walk is done. In vertex
+// order the hubs' counts share a few L2 lines that every walking warp would otherwise hit; no
+// crossing is looked for during the walk, so only the counts after it matter.
+constexpr int WALK_HUBS = 2048;
 __device__ __forceinline__ void fall_walk_v(const PeelArgs &a, WarpSmem &sm, int32_t pv_prev, int32_t prev_thrV,
                                             bool by_lvl, int64_t t0, int64_t nthreads, LaneStats &ls,
-                                            unsigned long long &ents, unsigned long long &decs) {
+                                            unsigned long long &ents, unsigned long long &decs,
+                                            unsigned *tab = nullptr) {
     const int lane = threadIdx.x & 31;
     // WILP groups of 32 vertices per warp per pass: all their count loads are issued first (one
     // vertex at a time would leave every lane waiting on a load per vertex), then each group's
@@ -1001,12 +1008,23 @@ __device__ __forceinline__ void fall_walk_v(const PeelArgs &a, WarpSmem &sm, int
                     if (y[u] < 0) continue;
                     ents++;
                     if (y[u] < a.pU && y[u] >= a.cU) {  // a U candidate
-                        cnt_dec_noret(a, y[u]);
+                        if (tab != nullptr && y[u] < WALK_HUBS) atomicAdd(&tab[y[u]], 1u);
+                        else cnt_dec_noret(a, y[u]);
                         decs++;
                     }
                 }
             }
             __syncwarp();
+        }
+    }
+    if (tab != nullptr) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < WALK_HUBS; i += blockDim.x) {
+            const unsigned v = tab[i];
+            if (v != 0u) {
+                cnt_sub_noret(a, i, (int)v);
+                tab[i] = 0u;
+            }
         }
     }
 }
