@@ -274,6 +274,7 @@ struct abcore_ctx {
     int init_blocks = 0;     // resident k_init blocks (occupancy x SMs)
     int scan_blocks = 0;     // resident k_scan blocks
     int expand_blocks = 0;   // resident k_expand blocks
+    int gather_blocks = 0;   // resident k_gather blocks
     size_t hub_smem = 0;     // dynamic shared memory k_round0_hub has been allowed so far
     BatchState *batch = nullptr;
     ServeState *serve = nullptr;

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256, 4) k_cascade(PeelArgs a) {
         atomicMax(&a.ctl->ph[1], t);
         if (a.trace && blockIdx.x < abc::TRACE_BLOCKS) a.trace[4 + 4 * abc::TRACE_SAMPLES + 2 * blockIdx.x] = t;
     }
-    k_cascade_emit(a, ok, gw, nw, lane);
+    if (a.emit == 2) k_cascade_emit(a, ok, gw, nw, lane);  // the gather is k_gather's
     if (a.phases) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -420,6 +420,17 @@ __device__ __forceinline__ void k_cascade_emit(const PeelArgs &a, int ok, int64_
             }
         }
     }
+}
+
+// The caller-order gather (emission 1) as a launch of its own after the cascade: its loads are
+// all coalesced, so a full-occupancy grid moves them faster than the cascade's. Skipped when the
+// cascade failed (the next peel then clears the removal bitmap).
+__global__ void __launch_bounds__(256) k_gather(PeelArgs a) {
+    abc::grid_dep_wait();
+    if (abc::ld_relaxed_i32(&a.ctl->err) != 0) return;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    k_cascade_emit(a, 1, gw, nw, threadIdx.x & 31);
 }
 
 // After a scatter: both masks from the survivor bitmap, 32 caller ids (one word) per thread
@@ -806,6 +817,15 @@ int peel_compute(abcore_ctx *ctx, int32_t alpha, int32_t beta, uint8_t *d_mask_u
     }
     ABC_CU(launch_k(pdl && prev_k, k_cascade, blocks, 256, ctx->stream, (size_t)0, a));
     ctx->stats.launches++;
+    if (a.emit == 1) {
+        if (ctx->gather_blocks <= 0) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather, 256, 0);
+            ctx->gather_blocks = std::max(per_sm, 1) * ctx->num_sms;
+        }
+        ABC_CU(launch_k(pdl, k_gather, ctx->gather_blocks, 256, ctx->stream, (size_t)0, a));
+        ctx->stats.launches++;
+    }
     if (a.emit == 2) {
         if (ctx->expand_blocks <= 0) {
             int per_sm = 0;
