@@ -441,27 +441,37 @@ __global__ void __launch_bounds__(256) k_expand(PeelArgs a) {
     abc::grid_dep_launch();
     abc::grid_dep_wait();
     const int64_t n = (int64_t)a.nU + a.nV, nw = (n + 31) / 32;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t bits = __ldcg(&a.sbits[w]);
-        if (bits != 0u) a.sbits[w] = 0u;
-        const int64_t i0 = w * 32;
-        // 4 bits -> 4 bytes of 0/1: the multiplier moves bit t to bit 8t, and nothing else lands
-        // on those four positions
-        uint32_t q[8];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    constexpr int EILP = 4;  // words per thread per pass, their loads in flight together
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w0 < nw; w0 += stride * EILP) {
+        uint32_t wb[EILP];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) q[k] = (((bits >> (4 * k)) & 0xfu) * 0x00204081u) & 0x01010101u;
-        uint8_t *dst = nullptr;
-        if (i0 + 32 <= a.nU) dst = a.mask_u + i0;
-        else if (i0 >= a.nU && i0 + 32 <= n) dst = a.mask_v + (i0 - a.nU);
-        if (dst != nullptr && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-            __stcs(&d4[0], make_uint4(q[0], q[1], q[2], q[3]));
-            __stcs(&d4[1], make_uint4(q[4], q[5], q[6], q[7]));
-        } else {
-            for (int j = 0; j < 32 && i0 + j < n; ++j) {
-                const uint8_t v = (uint8_t)((bits >> j) & 1u);
-                if (i0 + j < a.nU) a.mask_u[i0 + j] = v;
-                else a.mask_v[i0 + j - a.nU] = v;
+        for (int e = 0; e < EILP; ++e) wb[e] = w0 + e * stride < nw ? __ldcg(&a.sbits[w0 + e * stride]) : 0u;
+#pragma unroll
+        for (int e = 0; e < EILP; ++e) {
+            const int64_t w = w0 + e * stride;
+            if (w >= nw) break;
+            const uint32_t bits = wb[e];
+            if (bits != 0u) a.sbits[w] = 0u;
+            const int64_t i0 = w * 32;
+            // 4 bits -> 4 bytes of 0/1: the multiplier moves bit t to bit 8t, and nothing else
+            // lands on those four positions
+            uint32_t q[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = (((bits >> (4 * k)) & 0xfu) * 0x00204081u) & 0x01010101u;
+            uint8_t *dst = nullptr;
+            if (i0 + 32 <= a.nU) dst = a.mask_u + i0;
+            else if (i0 >= a.nU && i0 + 32 <= n) dst = a.mask_v + (i0 - a.nU);
+            if (dst != nullptr && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                __stcs(&d4[0], make_uint4(q[0], q[1], q[2], q[3]));
+                __stcs(&d4[1], make_uint4(q[4], q[5], q[6], q[7]));
+            } else {
+                for (int jj = 0; jj < 32 && i0 + jj < n; ++jj) {
+                    const uint8_t v = (uint8_t)((bits >> jj) & 1u);
+                    if (i0 + jj < a.nU) a.mask_u[i0 + jj] = v;
+                    else a.mask_v[i0 + jj - a.nU] = v;
+                }
             }
         }
     }
