@@ -88,8 +88,7 @@ struct BatchArgs {
 };
 
 // Compiled for two occupancies: three blocks an SM (80 registers a thread, some spilled) or two
-// (no spills, and room for the cascade's software-pipelined row loads); "blocks_per_sm" = 2
-// picks the second.
+// (no spills); "blocks_per_sm" = 2 picks the second.
 template <int MINB>
 __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
     __shared__ WarpSmem smem[BATCH_THREADS / 32];
@@ -165,7 +164,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
     if (prof) prof[prof_at(0, 1)] = abc::now_ns();
     // A failed cascade leaves its code in ctl->err. Every warp still reaches the barrier, so no
     // block waits on warps that left, and the barrier reports the error to all of them.
-    (void)abc::cascade_loop<(MINB < 3)>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
+    (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
     if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
     if (prof) prof[prof_at(0, 2)] = abc::now_ns();
     for (int j = 1; j < cd.nsteps; ++j) {
@@ -197,7 +196,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, MINB) k_batch(BatchArgs B) {
         }
         if (!abc::group_barrier(mem.bar, G, mem.ctl, false, B.timeout_ns)) goto out;
         if (prof) prof[prof_at(j, 1)] = abc::now_ns();
-        (void)abc::cascade_loop<(MINB < 3)>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
+        (void)abc::cascade_loop<false>(a, smem[wib], ls, grab_div, r == 0 && wib == 0);
         if (!abc::group_barrier(mem.bar, G, mem.ctl, true, B.timeout_ns)) goto out;
         if (prof) prof[prof_at(j, 2)] = abc::now_ns();
     }
