@@ -306,7 +306,8 @@ def test_round0_first_round_without_returns(mode):
     off, adj = oracle.build_csr(nU, nV, eu.numpy(), ev.numpy())
     core.set_param("round0", 1)
     core.set_param("mode", mode)
-    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8), (70, 3), (2, 150)]
+    # (the last three leave a layer, or both, without candidates: empty hub tables)
+    pairs = [(2, 3), (3, 2), (4, 4), (6, 2), (1, 9), (8, 8), (70, 3), (2, 150), (250, 2), (2, 250), (250, 250)]
     # variant 5 sums hub decrements in shared memory: no table, a table smaller than a warp, one
     # of a few rows' worth, and one larger than either candidate layer
     walks = [(v, 16384) for v in range(5)] + [(5, 0), (5, 7), (5, 64), (5, 16384)]
